@@ -1,0 +1,292 @@
+"""Benchmark of the two-beam FFT BPM hot path on GB300.
+
+A step is one pass of the whole hot path over one synthetic workload: the
+deformation factor c(x, z) from the displacement field, the per-channel
+propagator tables and coupling coefficients, the incident field, the resident
+split-step march of every channel, the reflectivities and the frequency-to-time
+assembly.  Default workload: deformed crystal, Nx = 4096, 2000 z steps, 1024
+frequency channels (8.39e9 cell-updates per step).  The metric is
+cell-updates per second (channel x transverse cell x z step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs under torchrun: every rank marches an independent instance of the
+same size (weak scaling); there is no data-path collective.  --impl reference
+times the FP64 CPU oracle on the host cores on a bounded channel sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2201_08500_gb300 import workloads  # noqa: E402
+
+METRIC = "BPM cell-updates/s (omega*x*z)"
+UNIT = "cell-updates/s"
+FP32_LANES_PER_SM = 128
+
+
+def flops_per_cell(n: int) -> float:
+    """Nominal FLOPs per cell-update: 4 FFTs at 5 N log2 N, 2 propagator
+    multiplies (12), the coupling (40)."""
+    return 20.0 * math.log2(n) + 52.0
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_sample(w, n_channels: int, n_threads: int):
+    """Time the FP64 oracle (as it stands) on n_channels channels of workload w."""
+    import oracle.oracle as orc
+    orc.build()
+    idx = np.linspace(0, w.n_ch - 1, n_channels).round().astype(int)
+    t0 = time.perf_counter()
+    orc.run(w, channels=idx, n_threads=n_threads)
+    dt = time.perf_counter() - t0
+    cells = n_channels * w.plane * w.nz
+    return cells / dt, dt, cells
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    w = workloads.deformed()
+    cores = os.cpu_count() or 1
+    n = max(1, min(w.n_ch, cores))
+    for _ in range(args.warmup):
+        oracle_sample(w.subset(range(0, w.n_ch, max(1, w.n_ch // n))), 1, 1)
+    vals = []
+    t_all = 0.0
+    for _ in range(args.steps):
+        v, dt, cells = oracle_sample(w, n, cores)
+        vals.append(v)
+        t_all += dt
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * w.cell_updates / value, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "nx": w.nx, "nz": w.nz, "channels": w.n_ch,
+                   "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{n} of {w.n_ch} channels, full {w.nz}-step march, "
+                                   f"per step; throughput scaled per cell-update"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+    from paper_2201_08500_gb300 import bpm
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    w = workloads.deformed(seed=2 + rank)
+    stream = torch.cuda.current_stream()
+    u_dev = torch.from_numpy(np.ascontiguousarray(w.u)).cuda()
+    plan = bpm.Plan(w.dims, w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.n_ch, stream=stream,
+                    zassenhaus=w.zassenhaus)
+    plan.set_timing(True)
+    omega = np.ascontiguousarray(w.omega)
+    S = np.ascontiguousarray(w.S)
+
+    def step(u):
+        plan.set_crystal(w.chi0, w.chih, w.chihb, w.theta_B, w.lambda_B, w.x_surface,
+                         w.thickness, u=u)
+        plan.set_pulse(omega, S, w.theta_i, w.x0, w.w0, w.zx, w.zR)
+        plan.run()
+
+    # L2 (129 MB) is flushed between timed steps by writing a 256 MB buffer
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    for _ in range(max(3, args.warmup)):
+        step(u_dev)
+    barrier()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    march_ms = []
+    barrier()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        step(u_dev)
+        ev[i][1].record(stream)
+        plan.sync()
+        march_ms.append(plan.stats()["march_ms"])
+    barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms_local = sum(step_ms) / len(step_ms)
+    t = torch.tensor([ms_local], device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    cells_per_rank = w.cell_updates
+    value = world * cells_per_rank / (ms * 1e-3)
+
+    # end to end through the C ABI with host buffers: pinned u in, R and the
+    # time response out, copies inside the timed region
+    u_pin = torch.from_numpy(np.ascontiguousarray(w.u)).pin_memory()
+    t_host = torch.empty((w.n_ch, w.plane), dtype=torch.complex128).pin_memory()
+    R = np.empty(w.n_ch)
+    e2e_ms = []
+    for i in range(max(2, min(args.steps, 5))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(u_pin)
+        plan.fetch(bpm.BPM_FIELD_EH_TIME, out=t_host)
+        R, _, _ = plan.reflectivity()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e = statistics.median(e2e_ms)
+    h2d = w.u.nbytes + omega.nbytes + S.nbytes
+    d2h = t_host.numel() * t_host.element_size() + 2 * R.nbytes
+
+    st = plan.stats()
+    n = w.nx
+    march_avg = statistics.mean(march_ms)
+    achieved = cells_per_rank * flops_per_cell(n) / (march_avg * 1e-3) / 1e12
+    props = torch.cuda.get_device_properties(local)
+    pk = measured_peaks()
+    sm_max = pk.get("sm_max_mhz", 2070.0)
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64 fields / f32 butterflies (f64 setup and time sum)",
+            "data": "synthetic",
+            "config": {"workload": w.name, "nx": w.nx, "nz": w.nz, "channels": w.n_ch,
+                       "crystal": "thermal bump u = A exp(-x'^2/w^2)(z/Z)^2",
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": f"{world} x independent instance"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": f"march_kernel<{n},{st['channels_per_block']}>",
+                         "flops_per_cell_update": flops_per_cell(n),
+                         "march_ms": march_avg,
+                         "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 "
+                                       f"x {sm_max:.0f} MHz"},
+            "e2e": {"value": world * cells_per_rank / (e2e * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": 5 * args.steps,
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline and world == 1:
+            cores = os.cpu_count() or 1
+            v, dt, cells = oracle_sample(w, max(1, min(cores, 16)), cores)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                    "sample": f"{max(1, min(cores, 16))} of {w.n_ch} channels, "
+                                              f"full {w.nz}-step march ({dt:.1f} s)"}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

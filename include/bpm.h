@@ -1,0 +1,176 @@
+/*
+ * bpm.h -- C ABI of the GB300-native two-beam FFT beam propagation method.
+ *
+ * Method: Krzywinski & Halavanau, "Time-dependent dynamical Bragg diffraction
+ * in deformed crystals by beam propagation method (BPM)", arXiv:2201.08500.
+ * For every frequency channel omega_i of an X-ray pulse, the transmitted and
+ * reflected slowly varying envelopes E0 (carrier exp(+i h x/2)) and Eh
+ * (carrier exp(-i h x/2)) are marched through the crystal in z (Eq. fov10):
+ * each step Fourier-transforms both envelopes along x (x and y in 3D),
+ * multiplies them by the tilted angular propagators (Eq. fov4 and the shifted
+ * operators p+- defined after Eq. fov10), transforms back and couples them
+ * pointwise through the first Jacobi-Anger terms of the susceptibility step
+ * (Eqs. fov9, fov11, fov12) with the Zassenhaus-like factor and the
+ * deformation phase exp(+-i h u) (Eq. Authier).  The time response is the
+ * channel sum of Section 3.3 (text after Eq. ref:tdp).
+ *
+ * Conventions (all calls):
+ *  - Units are SI; scalars are double precision.
+ *  - Grid: x_j = j dx (j < nx); in 3D y_r = (r - ny/2) dy.  Fields are row-major
+ *    [channel][y][x] complex64 (interleaved re, im float32).
+ *  - Every call returns a bpm_status and never throws or aborts.  On error the
+ *    plan keeps its previous state and bpm_last_error() describes the failure.
+ *  - Ownership: the caller owns the CUDA stream and every buffer it passes.
+ *    Host arrays are copied before the call returns.  Device pointers passed
+ *    in (u_field with u_on_device=1, set_fields/fetch with on_device=1) must
+ *    stay valid until the plan's stream has consumed them.  The plan owns its
+ *    internal device memory (tables, fields, outputs) until bpm_plan_destroy.
+ *  - Threads: a plan is used by one host thread at a time.  Distinct plans may
+ *    be used concurrently.  Device work is asynchronous on the plan's stream;
+ *    bpm_sync() waits for it and reports device-side failures.
+ *  - There is no CPU fallback: without a usable GB300 (sm_103a) device the
+ *    calls return BPM_ERR_CUDA or BPM_ERR_UNSUPPORTED.
+ */
+#ifndef BPM_H_
+#define BPM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BPM_API __attribute__((visibility("default")))
+
+typedef enum {
+  BPM_OK = 0,
+  BPM_ERR_INVALID_ARG = 1, /* bad size, pointer, ordering of calls or physics input */
+  BPM_ERR_OOM = 2,         /* device allocation failed / batch has no room yet     */
+  BPM_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed          */
+  BPM_ERR_UNSUPPORTED = 4, /* grid size or option this build does not implement    */
+  BPM_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up                   */
+  BPM_ERR_STATE = 6,       /* call out of order (e.g. run before set_pulse)        */
+  BPM_ERR_CANCELLED = 7    /* batch entry was cancelled                            */
+} bpm_status;
+
+typedef struct bpm_plan_s* bpm_plan;
+
+/* Transverse grid and march.  dims = 2: (x, z), ny must be 1; dims = 3: (x, y, z).
+ * nx (and ny) are powers of two: 256..8192 for dims = 2, 64..1024 for dims = 3.
+ * split_order: 1 (first-order splitting a1 = b1 = 1 of Eq. split-op; the only
+ * order implemented).  zassenhaus: 1 applies exp(D2 dz-hat^2/2),
+ * D2 = (chi_h/2/cos alpha)^2, to the zeroth Jacobi-Anger term (Section 2,
+ * equation after Eq. split-op); 0 leaves it out. */
+typedef struct {
+  int32_t dims;
+  int32_t nx, ny, nz;
+  double dx, dy, dz;
+  int32_t split_order;
+  int32_t zassenhaus;
+} bpm_grid;
+
+/* Creates a plan for n_channels frequency channels on cuda_stream (a
+ * cudaStream_t; NULL = legacy default stream).  Validates the grid and
+ * allocates the plan's device buffers.
+ * Errors: INVALID_ARG (null pointers, n_channels < 1, non-positive steps),
+ * UNSUPPORTED (sizes outside the list above, split_order != 1), OOM, CUDA. */
+BPM_API bpm_status bpm_plan_create(const bpm_grid* grid, int n_channels, void* cuda_stream,
+                                   bpm_plan* out);
+
+/* Crystal (Section 2, Eqs. fov8, fov11, fov12, Eq. Authier; geometry of the
+ * symmetric Bragg slab described before Section 3): susceptibilities chi0,
+ * chi_h, chi_hbar (taken literally as complex numbers); Bragg angle theta_B
+ * (rad, 0 <= theta_B < 85 deg, Section 2 notes the method fails near
+ * back-scattering) and wavelength lambda_B (m) give h = 4 pi sin(theta_B)/lambda_B;
+ * the slab occupies x_surface <= x < x_surface + thickness (all z); u_field is
+ * the x-component of the displacement in metres, [nz][ny][nx] float64, or NULL
+ * for a perfect crystal; u_on_device says whether u_field is a device pointer.
+ * Builds the per-cell factor Pi * exp(+i h u) on the device (FP64 phase).
+ * Errors: INVALID_ARG, OOM, CUDA. */
+BPM_API bpm_status bpm_set_crystal(bpm_plan plan, double chi0_re, double chi0_im, double chih_re,
+                                   double chih_im, double chihbar_re, double chihbar_im,
+                                   double theta_B, double lambda_B, double x_surface,
+                                   double thickness, const double* u_field, int u_on_device);
+
+/* Incident pulse (Section 3.1 beam, Eq. ref:tdp and the frequency decomposition
+ * after it): omega[n_channels] angular frequencies (rad/s, uniformly spaced for
+ * the time assembly), weight_re_im[2*n_channels] complex spectral amplitudes
+ * S_i, incidence angle theta_i (rad), beam centre x0 (m), waist W0 (m),
+ * distance to the waist zx and Rayleigh range zR (m).  Per channel the device
+ * builds the propagator tables, the coupling coefficients and the incident
+ * field A+ = S_i g(x, y) exp(i (k_i sin theta_i - h/2) x), A- = 0, and resets
+ * the march to z = 0.  Requires bpm_set_crystal first.
+ * Errors: INVALID_ARG (null arrays, k_i <= h/2), STATE, OOM, CUDA. */
+BPM_API bpm_status bpm_set_pulse(bpm_plan plan, const double* omega, const double* weight_re_im,
+                                 double theta_i, double x0, double w0, double zx, double zR);
+
+/* Replaces both envelopes (complex64 [n_channels][ny][nx]) and sets the march
+ * position to z_step (0 <= z_step <= nz): resumes from a checkpoint taken with
+ * bpm_fetch_fields.  Reflectivities stay normalised to the incident field of
+ * the last bpm_set_pulse.  Errors: INVALID_ARG, STATE, CUDA. */
+BPM_API bpm_status bpm_set_fields(bpm_plan plan, const void* e0, const void* eh, int z_step,
+                                  int on_device);
+
+/* Advances every channel n_steps split steps (Eq. fov10) from the current z,
+ * then computes per-channel reflectivity R_i = sum|A-|^2 / sum|A+(z=0)|^2 and
+ * transmissivity T_i, and, when the march has reached nz, the time response
+ * (BPM_FIELD_EH_TIME).  Asynchronous on the plan's stream.
+ * Errors: INVALID_ARG (n_steps < 0 or past nz), STATE (no pulse), CUDA. */
+BPM_API bpm_status bpm_run(bpm_plan plan, int n_steps);
+
+/* Waits for the plan's stream and reports device status: TIMEOUT if a bounded
+ * device wait gave up, CUDA on an asynchronous error. */
+BPM_API bpm_status bpm_sync(bpm_plan plan);
+
+enum {
+  BPM_FIELD_E0 = 0,     /* complex64  [n_channels][ny][nx], current z              */
+  BPM_FIELD_EH = 1,     /* complex64  [n_channels][ny][nx], current z              */
+  BPM_FIELD_EH_TIME = 2 /* complex128 [n_time = n_channels][ny][nx]: psi_h(t_j, x) =
+                           d_omega sum_i A-(omega_i, x) exp(-2 pi i (i - n/2) j / n),
+                           t_j = 2 pi j / (n d_omega), envelope about omega_{n/2}  */
+};
+
+/* Copies one output into dst (bytes must equal its exact size) on the plan's
+ * stream, then waits for the copy.  dst_on_device selects a device or host
+ * destination.  Errors: INVALID_ARG (size/which), STATE (EH_TIME before the
+ * march reached nz), CUDA, TIMEOUT. */
+BPM_API bpm_status bpm_fetch_fields(bpm_plan plan, int which, void* dst, size_t bytes,
+                                    int dst_on_device);
+
+/* Host copies of R[n_channels], T[n_channels] (either may be NULL) and the
+ * integrated reflectivity R_int = d_omega * sum_i R_i (d_omega = omega_1 -
+ * omega_0; 1 for a single channel).  Waits for the stream. */
+BPM_API bpm_status bpm_fetch_reflectivity(bpm_plan plan, double* R, double* T, double* R_int);
+
+/* Timing and launch accounting of the most recent bpm_run (after bpm_sync):
+ * march_ms is the device time of the march kernel(s) measured with CUDA events
+ * on the plan's stream (0 unless enabled with bpm_set_timing), launches is the
+ * number of kernels bpm_run enqueued. */
+typedef struct {
+  double march_ms;
+  int32_t launches;
+  int32_t march_launches;
+  int32_t threads_per_channel;
+  int32_t channels_per_block;
+  int32_t blocks;
+  int32_t smem_bytes;
+} bpm_stats;
+BPM_API bpm_status bpm_set_timing(bpm_plan plan, int enable);
+BPM_API bpm_status bpm_get_stats(bpm_plan plan, bpm_stats* out);
+
+/* Message of the last failed call on this plan (plan = NULL: the last failed
+ * bpm_plan_create / batch call of this thread).  Never NULL. */
+BPM_API const char* bpm_last_error(bpm_plan plan);
+
+/* Frees the plan and its device memory after its stream has drained.  NULL is a no-op. */
+BPM_API void bpm_plan_destroy(bpm_plan plan);
+
+/* Library version string (build tag and target architecture). */
+BPM_API const char* bpm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BPM_H_ */

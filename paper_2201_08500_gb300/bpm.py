@@ -1,0 +1,232 @@
+"""Thin ctypes binding of libbpm (include/bpm.h): argument marshalling only.
+
+Every step of the BPM runs in the CUDA library; this module converts numpy
+arrays / torch tensors to pointers and status codes to exceptions.  There is
+no fallback: if libbpm.so cannot be loaded, or the device is not a GB300
+(sm_103a), the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbpm.so")
+
+BPM_FIELD_E0, BPM_FIELD_EH, BPM_FIELD_EH_TIME = 0, 1, 2
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "UNSUPPORTED", 5: "TIMEOUT",
+          6: "STATE", 7: "CANCELLED"}
+
+# Every symbol include/bpm.h declares (checked by the CPU test suite).
+EXPORTS = ("bpm_plan_create", "bpm_set_crystal", "bpm_set_pulse", "bpm_set_fields", "bpm_run",
+           "bpm_sync", "bpm_fetch_fields", "bpm_fetch_reflectivity", "bpm_set_timing",
+           "bpm_get_stats", "bpm_last_error", "bpm_plan_destroy", "bpm_version")
+
+
+class BpmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("nz", ctypes.c_int32), ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("dz", ctypes.c_double), ("split_order", ctypes.c_int32),
+                ("zassenhaus", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("march_ms", ctypes.c_double), ("launches", ctypes.c_int32),
+                ("march_launches", ctypes.c_int32), ("threads_per_channel", ctypes.c_int32),
+                ("channels_per_block", ctypes.c_int32), ("blocks", ctypes.c_int32),
+                ("smem_bytes", ctypes.c_int32)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+
+
+def load(path: str = LIB_PATH):
+    """Load libbpm.so (raises if it is missing: build it with __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"{path} is missing; build the CUDA library first "
+                                "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = ctypes.CDLL(path)
+    sig = {
+        "bpm_plan_create": ([ctypes.POINTER(Grid), _I, _P, ctypes.POINTER(_P)], _I),
+        "bpm_set_crystal": ([_P] + [_D] * 10 + [_P, _I], _I),
+        "bpm_set_pulse": ([_P, _P, _P, _D, _D, _D, _D, _D], _I),
+        "bpm_set_fields": ([_P, _P, _P, _I, _I], _I),
+        "bpm_run": ([_P, _I], _I),
+        "bpm_sync": ([_P], _I),
+        "bpm_fetch_fields": ([_P, _I, _P, ctypes.c_size_t, _I], _I),
+        "bpm_fetch_reflectivity": ([_P, _P, _P, _P], _I),
+        "bpm_set_timing": ([_P, _I], _I),
+        "bpm_get_stats": ([_P, ctypes.POINTER(Stats)], _I),
+        "bpm_last_error": ([_P], ctypes.c_char_p),
+        "bpm_plan_destroy": ([_P], None),
+        "bpm_version": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def version() -> str:
+    return load().bpm_version().decode()
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _is_device(a) -> bool:
+    return hasattr(a, "is_cuda") and bool(a.is_cuda)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+class Plan:
+    """One BPM problem (crystal + pulse, n_channels frequency channels) on one GPU."""
+
+    def __init__(self, dims, nx, ny, nz, dx, dy, dz, n_channels, stream=None, zassenhaus=1,
+                 split_order=1):
+        self._L = load()
+        self.dims, self.nx, self.ny, self.nz = int(dims), int(nx), int(ny), int(nz)
+        self.n_channels = int(n_channels)
+        self.plane = self.nx * (self.ny if self.dims == 3 else 1)
+        g = Grid(self.dims, self.nx, self.ny if self.dims == 3 else 1, self.nz, float(dx),
+                 float(dy), float(dz), int(split_order), int(zassenhaus))
+        h = _P()
+        self._keep = []
+        self._h = None
+        st = self._L.bpm_plan_create(ctypes.byref(g), self.n_channels, _stream_handle(stream),
+                                     ctypes.byref(h))
+        if st != 0:
+            raise BpmError(st, self._L.bpm_last_error(None).decode())
+        self._h = h
+
+    # -- helpers
+    def _check(self, st):
+        if st != 0:
+            raise BpmError(st, self._L.bpm_last_error(self._h).decode())
+
+    def close(self):
+        if self._h is not None:
+            self._L.bpm_plan_destroy(self._h)
+            self._h = None
+            self._keep = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- API
+    def set_crystal(self, chi0, chih, chihb, theta_B, lambda_B, x_surface, thickness, u=None):
+        if u is not None and not _is_device(u):
+            u = np.ascontiguousarray(u, dtype=np.float64)
+            if u.size != self.nz * self.plane:
+                raise ValueError("u must hold nz * ny * nx float64 values")
+        chi0, chih, chihb = complex(chi0), complex(chih), complex(chihb)
+        self._check(self._L.bpm_set_crystal(
+            self._h, chi0.real, chi0.imag, chih.real, chih.imag, chihb.real, chihb.imag,
+            float(theta_B), float(lambda_B), float(x_surface), float(thickness), _ptr(u),
+            1 if _is_device(u) else 0))
+        if _is_device(u):
+            self._keep = [u]
+
+    def set_pulse(self, omega, S, theta_i, x0, w0, zx=0.0, zR=1.0):
+        omega = np.ascontiguousarray(omega, dtype=np.float64)
+        S = np.ascontiguousarray(S, dtype=np.complex128)
+        if omega.size != self.n_channels or S.size != self.n_channels:
+            raise ValueError("omega and S need one entry per channel")
+        self._check(self._L.bpm_set_pulse(self._h, _ptr(omega), _ptr(S), float(theta_i),
+                                          float(x0), float(w0), float(zx), float(zR)))
+
+    def set_fields(self, e0, eh, z_step: int):
+        dev = _is_device(e0)
+        if not dev:
+            e0 = np.ascontiguousarray(e0, dtype=np.complex64)
+            eh = np.ascontiguousarray(eh, dtype=np.complex64)
+        self._check(self._L.bpm_set_fields(self._h, _ptr(e0), _ptr(eh), int(z_step),
+                                           1 if dev else 0))
+
+    def run(self, n_steps: int | None = None):
+        self._check(self._L.bpm_run(self._h, self.nz if n_steps is None else int(n_steps)))
+
+    def sync(self):
+        self._check(self._L.bpm_sync(self._h))
+
+    def fetch(self, which: int, out=None):
+        shape = (self.n_channels, self.plane)
+        if out is None:
+            dt = np.complex128 if which == BPM_FIELD_EH_TIME else np.complex64
+            out = np.empty(shape, dt)
+        nbytes = out.numel() * out.element_size() if hasattr(out, "numel") else out.nbytes
+        self._check(self._L.bpm_fetch_fields(self._h, int(which), _ptr(out), nbytes,
+                                             1 if _is_device(out) else 0))
+        return out
+
+    def e0(self):
+        return self.fetch(BPM_FIELD_E0)
+
+    def eh(self):
+        return self.fetch(BPM_FIELD_EH)
+
+    def eh_time(self):
+        return self.fetch(BPM_FIELD_EH_TIME)
+
+    def reflectivity(self):
+        R = np.empty(self.n_channels, np.float64)
+        T = np.empty(self.n_channels, np.float64)
+        rint = ctypes.c_double()
+        self._check(self._L.bpm_fetch_reflectivity(self._h, _ptr(R), _ptr(T), ctypes.byref(rint)))
+        return R, T, rint.value
+
+    def set_timing(self, enable: bool = True):
+        self._check(self._L.bpm_set_timing(self._h, 1 if enable else 0))
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(self._L.bpm_get_stats(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+
+def plan_from_workload(w, stream=None, u=None) -> Plan:
+    """Create a plan and load the crystal and the pulse of a workload record.
+    u overrides w.u (e.g. with a device tensor)."""
+    p = Plan(w.dims, w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.n_ch, stream=stream,
+             zassenhaus=w.zassenhaus)
+    p.set_crystal(w.chi0, w.chih, w.chihb, w.theta_B, w.lambda_B, w.x_surface, w.thickness,
+                  u=w.u if u is None else u)
+    p.set_pulse(w.omega, w.S, w.theta_i, w.x0, w.w0, w.zx, w.zR)
+    return p

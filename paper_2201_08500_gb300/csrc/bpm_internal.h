@@ -1,0 +1,66 @@
+// Internal declarations shared by the host runtime and the kernel translation
+// units of libbpm.  Not part of the public ABI (include/bpm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bpm {
+
+// Number of complex elements each thread holds per envelope in the resident
+// march kernel: one radix-16 butterfly group per thread per stage.
+constexpr int kElemsPerThread = 16;
+
+// Coupling coefficients of Eq. fov10 for one channel, FP32.  a is split into
+// hi + lo parts so that its systematic rounding does not accumulate over the
+// march; b+ (Eh -> E0) and b- (E0 -> Eh) are used once per step and stay FP32.
+struct ChannelCoef {
+  float2 a_hi, a_lo;
+  float2 bp, bm;
+};
+
+// Arguments of the resident split-step march kernel (one 1D plan).
+struct MarchArgs {
+  const float4* tables;      // [n_ch][2][16][T] {hi.re, hi.im, lo.re, lo.im}; env 0 = E0, 1 = Eh
+  const ChannelCoef* coef;   // [n_ch]
+  const float2* twiddle;     // [N] exp(-2 pi i k / N), FP32 correctly rounded
+  const float2* cfield;      // [nz][N] Pi(x, z) exp(+i h u(x, z)); 0 outside the crystal
+  float2* e0;                // [n_ch][N]
+  float2* eh;                // [n_ch][N]
+  const double* inc_norm;    // [n_ch] sum |A+(z=0)|^2
+  double* refl;              // [n_ch] R
+  double* trans;             // [n_ch] T
+  int n_ch;
+  int z0;
+  int n_steps;
+};
+
+// Per-plan device pointers used by the setup kernels.
+struct SetupArgs {
+  int nx, ny, nz, n_ch, dims;
+  double dx, dy, dz;
+  double h;                  // reciprocal-lattice vector
+  double chi0_re, chi0_im, chih_re, chih_im, chihb_re, chihb_im;
+  int zassenhaus;
+  double x_surface, x_end;   // slab [x_surface, x_end)
+  double theta_i, x0, w0, zx, zR;
+};
+
+// Launchers (bpm_march.cu).  Return cudaSuccess or the launch error.
+int march_threads_per_channel(int n);
+int march_max_group(int n);
+size_t march_smem_bytes(int n, int group);
+cudaError_t launch_march(int n, int group, int blocks, const MarchArgs& a, cudaStream_t s);
+
+// Setup launchers (bpm_setup.cu).
+cudaError_t launch_deformation(const SetupArgs& sa, const double* u_dev, float2* cfield,
+                               cudaStream_t s);
+cudaError_t launch_tables(const SetupArgs& sa, const double* omega, const double* gain,
+                          const int* rev, float4* tables, ChannelCoef* coef, int* bad,
+                          cudaStream_t s);
+cudaError_t launch_incident(const SetupArgs& sa, const double* omega, const double2* weight,
+                            float2* e0, float2* eh, double* inc_norm, cudaStream_t s);
+cudaError_t launch_omega_to_t(int n_ch, long long plane, double domega, const float2* eh,
+                              double2* out, cudaStream_t s);
+
+}  // namespace bpm

@@ -1,0 +1,44 @@
+"""CPU checks of the C-ABI boundary: the library builds, loads and exports every
+symbol include/bpm.h declares.  No compute call is made (no GPU here)."""
+import os
+import re
+
+import pytest
+
+from paper_2201_08500_gb300 import bpm
+from paper_2201_08500_gb300 import build as libbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "bpm.h")).read()
+    return sorted(set(re.findall(r"BPM_API\s+[\w\s\*]+?\b(bpm_\w+)\s*\(", txt)))
+
+
+def test_header_declares_the_binding_exports():
+    assert sorted(bpm.EXPORTS) == declared_symbols()
+
+
+def test_library_builds_loads_and_exports_every_symbol():
+    try:
+        libbuild.nvcc()
+    except RuntimeError:
+        pytest.skip("no nvcc")
+    path = libbuild.build()
+    L = bpm.load(path)
+    for name in declared_symbols():
+        assert hasattr(L, name), name
+    assert "sm_103a" in bpm.version()
+
+
+def test_error_path_without_plan_is_reported():
+    try:
+        L = bpm.load(libbuild.build())
+    except RuntimeError:
+        pytest.skip("no nvcc")
+    grid = bpm.Grid(2, 300, 1, 10, 1e-6, 0.0, 1e-6, 1, 1)
+    h = bpm._P()
+    st = L.bpm_plan_create(bpm.ctypes.byref(grid), 0, None, bpm.ctypes.byref(h))
+    assert st == 1  # INVALID_ARG: n_channels < 1 is rejected before any device call
+    assert b"n_channels" in L.bpm_last_error(None)

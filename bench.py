@@ -127,7 +127,7 @@ def oracle_sample(w, n_channels: int, n_threads: int):
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
-    w = workloads.deformed()
+    w = workloads.deformed(n_ch=args.channels, nz=args.nz)
     cores = os.cpu_count() or 1
     n = max(1, min(w.n_ch, cores))
     for _ in range(args.warmup):
@@ -162,6 +162,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--channels", type=int, default=1024,
+                    help="channels of the deformed workload (profiling: a smaller instance)")
+    ap.add_argument("--nz", type=int, default=2000, help="z steps of the deformed workload")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if args.impl == "reference":
@@ -181,7 +184,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    w = workloads.deformed(seed=2 + rank)
+    w = workloads.deformed(n_ch=args.channels, nz=args.nz, seed=2 + rank)
     stream = torch.cuda.current_stream()
     u_dev = torch.from_numpy(np.ascontiguousarray(w.u)).cuda()
     plan = bpm.Plan(w.dims, w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.n_ch, stream=stream,

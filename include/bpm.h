@@ -169,6 +169,76 @@ BPM_API void bpm_plan_destroy(bpm_plan plan);
 /* Library version string (build tag and target architecture). */
 BPM_API const char* bpm_version(void);
 
+/* Device bytes a plan of this grid and channel count allocates (host_u = 1 adds
+ * the staging buffer used when bpm_set_crystal receives a host displacement
+ * field).  Used for admission by device memory.  0 on invalid input. */
+BPM_API size_t bpm_plan_bytes(const bpm_grid* grid, int n_channels, int host_u);
+
+/* ---------------------------------------------------------------------------
+ * Batches and continuous batching.  The channels of all plans of a batch are
+ * independent stationary problems (Section 3.3: "N stationary tasks"), so one
+ * persistent launch marches them together: work items (plan, group of
+ * channels) are taken from a device queue, longest first, by blocks that run
+ * the resident march of the item's transform size.  Plans keep their fields
+ * on the device between rounds.  Batches take 2D plans (dims = 2).
+ * ------------------------------------------------------------------------- */
+typedef struct bpm_batch_s* bpm_batch;
+
+/* Creates a batch executing on cuda_stream.  hbm_budget_bytes > 0 bounds the
+ * sum of bpm_plan_bytes of the admitted, unfinished plans (0 = unbounded).
+ * Errors: INVALID_ARG, CUDA. */
+BPM_API bpm_status bpm_batch_create(size_t hbm_budget_bytes, void* cuda_stream, bpm_batch* out);
+
+/* Admits a plan whose crystal and pulse are set; it is marched from its current
+ * z to nz by later rounds.  The plan's stream is replaced by the batch stream
+ * (its pending work is ordered before the batch).  The caller keeps ownership
+ * and destroys the plan after its ticket reports done (or after cancel).
+ * Errors: OOM (budget exhausted: not admitted, retry later), STATE (no pulse,
+ * already admitted), UNSUPPORTED (3D plan), INVALID_ARG. */
+BPM_API bpm_status bpm_batch_submit(bpm_batch b, bpm_plan plan, uint64_t* ticket);
+
+/* Enqueues one round: every admitted, unfinished plan advances
+ * min(chunk_steps, nz - z) steps in one persistent launch (plus a sibling
+ * launch for Nx = 8192 on a forked stream); plans that reach nz then get their
+ * reflectivity and time response and a completion event.  Asynchronous.
+ * Plans admitted after this call join the next round (continuous batching).
+ * Errors: INVALID_ARG, CUDA. */
+BPM_API bpm_status bpm_batch_step(bpm_batch b, int chunk_steps);
+
+/* One round that takes every admitted plan to nz (a single persistent launch
+ * per queue).  Asynchronous. */
+BPM_API bpm_status bpm_batch_run(bpm_batch b);
+
+/* Runs the whole hot path of every admitted plan as one CUDA graph: the
+ * deformation factor, tables and incident field from the inputs stored by
+ * bpm_set_crystal / bpm_set_pulse (device pointers must still be valid), one
+ * round to nz and the time responses.  Captured on first use and whenever the
+ * set of plans changes, replayed otherwise.  Asynchronous. */
+BPM_API bpm_status bpm_batch_run_graph(bpm_batch b);
+
+/* Non-blocking completion test of a ticket; done = 1 once its results can be
+ * fetched from its plan (the plan's budget share is then released).
+ * Errors: CANCELLED, INVALID_ARG (unknown ticket), CUDA. */
+BPM_API bpm_status bpm_batch_poll(bpm_batch b, uint64_t ticket, int* done);
+
+/* Removes an unfinished plan from later rounds (waits for rounds already
+ * enqueued).  Errors: STATE (already finishing), INVALID_ARG. */
+BPM_API bpm_status bpm_batch_cancel(bpm_batch b, uint64_t ticket);
+
+/* Waits for all enqueued rounds. */
+BPM_API bpm_status bpm_batch_sync(bpm_batch b);
+
+/* Admitted unfinished plans, their bytes, rounds enqueued so far and the item
+ * counts [small, Nx = 8192] of the last round (any pointer may be NULL). */
+BPM_API bpm_status bpm_batch_info(bpm_batch b, int* active, size_t* used_bytes, int* rounds,
+                                  int* last_items);
+
+/* Message of the last failed call on this batch (NULL: of this thread). */
+BPM_API const char* bpm_batch_last_error(bpm_batch b);
+
+/* Waits for the batch stream and frees the batch (not the plans). */
+BPM_API void bpm_batch_destroy(bpm_batch b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,7 +22,10 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "UNSUPPORTED", 5: "
 # Every symbol include/bpm.h declares (checked by the CPU test suite).
 EXPORTS = ("bpm_plan_create", "bpm_set_crystal", "bpm_set_pulse", "bpm_set_fields", "bpm_run",
            "bpm_sync", "bpm_fetch_fields", "bpm_fetch_reflectivity", "bpm_set_timing",
-           "bpm_get_stats", "bpm_last_error", "bpm_plan_destroy", "bpm_version")
+           "bpm_get_stats", "bpm_last_error", "bpm_plan_destroy", "bpm_version", "bpm_plan_bytes",
+           "bpm_batch_create", "bpm_batch_submit", "bpm_batch_step", "bpm_batch_run",
+           "bpm_batch_run_graph", "bpm_batch_poll", "bpm_batch_cancel", "bpm_batch_sync",
+           "bpm_batch_info", "bpm_batch_last_error", "bpm_batch_destroy")
 
 
 class BpmError(RuntimeError):
@@ -74,6 +77,19 @@ def load(path: str = LIB_PATH):
         "bpm_last_error": ([_P], ctypes.c_char_p),
         "bpm_plan_destroy": ([_P], None),
         "bpm_version": ([], ctypes.c_char_p),
+        "bpm_plan_bytes": ([ctypes.POINTER(Grid), _I, _I], ctypes.c_size_t),
+        "bpm_batch_create": ([ctypes.c_size_t, _P, ctypes.POINTER(_P)], _I),
+        "bpm_batch_submit": ([_P, _P, ctypes.POINTER(ctypes.c_uint64)], _I),
+        "bpm_batch_step": ([_P, _I], _I),
+        "bpm_batch_run": ([_P], _I),
+        "bpm_batch_run_graph": ([_P], _I),
+        "bpm_batch_poll": ([_P, ctypes.c_uint64, ctypes.POINTER(_I)], _I),
+        "bpm_batch_cancel": ([_P, ctypes.c_uint64], _I),
+        "bpm_batch_sync": ([_P], _I),
+        "bpm_batch_info": ([_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_size_t),
+                            ctypes.POINTER(_I), ctypes.POINTER(_I * 2)], _I),
+        "bpm_batch_last_error": ([_P], ctypes.c_char_p),
+        "bpm_batch_destroy": ([_P], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -230,3 +246,82 @@ def plan_from_workload(w, stream=None, u=None) -> Plan:
                   u=w.u if u is None else u)
     p.set_pulse(w.omega, w.S, w.theta_i, w.x0, w.w0, w.zx, w.zR)
     return p
+
+
+def plan_bytes(dims, nx, ny, nz, n_channels, host_u=False) -> int:
+    """Device bytes a plan allocates (admission by device memory)."""
+    g = Grid(int(dims), int(nx), int(ny) if int(dims) == 3 else 1, int(nz), 1.0, 1.0, 1.0, 1, 1)
+    return int(load().bpm_plan_bytes(ctypes.byref(g), int(n_channels), 1 if host_u else 0))
+
+
+class Batch:
+    """Many plans marched by one persistent work-queue launch per round
+    (continuous batching: plans submitted between rounds join the next one)."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, stream=None):
+        self._L = load()
+        h = _P()
+        self._h = None
+        st = self._L.bpm_batch_create(int(hbm_budget_bytes), _stream_handle(stream),
+                                      ctypes.byref(h))
+        if st != 0:
+            raise BpmError(st, self._L.bpm_batch_last_error(None).decode())
+        self._h = h
+
+    def _check(self, st):
+        if st != 0:
+            raise BpmError(st, self._L.bpm_batch_last_error(self._h).decode())
+
+    def submit(self, plan: Plan) -> int:
+        """Admit a plan; raises BpmError with status 2 (OOM) if the budget is full."""
+        t = ctypes.c_uint64()
+        self._check(self._L.bpm_batch_submit(self._h, plan._h, ctypes.byref(t)))
+        return int(t.value)
+
+    def try_submit(self, plan: Plan):
+        t = ctypes.c_uint64()
+        st = self._L.bpm_batch_submit(self._h, plan._h, ctypes.byref(t))
+        if st == 2:
+            return None
+        self._check(st)
+        return int(t.value)
+
+    def step(self, chunk_steps: int):
+        self._check(self._L.bpm_batch_step(self._h, int(chunk_steps)))
+
+    def run(self):
+        self._check(self._L.bpm_batch_run(self._h))
+
+    def run_graph(self):
+        self._check(self._L.bpm_batch_run_graph(self._h))
+
+    def poll(self, ticket: int) -> bool:
+        d = _I()
+        self._check(self._L.bpm_batch_poll(self._h, ctypes.c_uint64(ticket), ctypes.byref(d)))
+        return bool(d.value)
+
+    def cancel(self, ticket: int):
+        self._check(self._L.bpm_batch_cancel(self._h, ctypes.c_uint64(ticket)))
+
+    def sync(self):
+        self._check(self._L.bpm_batch_sync(self._h))
+
+    def info(self) -> dict:
+        a, r = _I(), _I()
+        u = ctypes.c_size_t()
+        it = (_I * 2)()
+        self._check(self._L.bpm_batch_info(self._h, ctypes.byref(a), ctypes.byref(u),
+                                           ctypes.byref(r), ctypes.byref(it)))
+        return dict(active=a.value, used_bytes=u.value, rounds=r.value,
+                    last_items=(it[0], it[1]))
+
+    def close(self):
+        if self._h is not None:
+            self._L.bpm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

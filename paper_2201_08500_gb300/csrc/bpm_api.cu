@@ -7,6 +7,7 @@
 // caller's stream.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -153,6 +154,9 @@ const DeviceInfo& device_info() {
     d.sm_count = prop.multiProcessorCount;
     d.cc = prop.major * 10 + prop.minor;
     d.ok = true;
+    if (d.cc == 103)
+      d.ok = march_set_attributes() == cudaSuccess && batch_set_attributes() == cudaSuccess &&
+             setup_set_attributes() == cudaSuccess;
   }
   cache[dev] = d;
   return cache[dev];
@@ -189,6 +193,8 @@ struct bpm_plan_s {
   double2* eh_time = nullptr;
   int* dflag = nullptr;
   double* u_tmp = nullptr;
+  const double* u_dev = nullptr;  // displacement used by the deformation setup (may be null)
+  size_t bytes = 0;               // device bytes owned by the plan
 
   int group = 1, blocks = 0;
   bool timing = false;
@@ -239,6 +245,35 @@ void free_plan_buffers(bpm_plan p) {
 
 bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
+// Device bytes a 1D plan allocates (fields, tables, deformation factor, outputs).
+size_t plan_bytes(const bpm_grid& g, int n_ch) {
+  const size_t plane = size_t(g.nx) * (g.dims == 3 ? g.ny : 1);
+  const size_t nf = size_t(n_ch) * plane;
+  size_t b = 0;
+  b += size_t(g.nz) * plane * sizeof(float2);      // deformation factor
+  b += 2 * nf * sizeof(float2);                    // E0, Eh
+  b += size_t(n_ch) * 2 * g.nx * sizeof(float4);   // propagator tables
+  b += size_t(n_ch) * sizeof(ChannelCoef);
+  b += size_t(g.nx) * (sizeof(float2) + sizeof(int) + sizeof(double));
+  b += size_t(n_ch) * (5 * sizeof(double) + sizeof(double2));
+  b += nf * sizeof(double2);                       // time response
+  return b;
+}
+
+// Re-derive the deformation factor of the plan from its stored displacement.
+cudaError_t enqueue_crystal(bpm_plan p) { return launch_deformation(p->sa, p->u_dev, p->cfield, p->stream); }
+
+// Tables, coefficients and incident field from the stored pulse; march back to z = 0.
+cudaError_t enqueue_pulse(bpm_plan p) {
+  cudaError_t e = launch_tables(p->sa, p->omega, p->gain, p->rev, p->tables, p->coef, p->dflag,
+                                p->stream);
+  if (e != cudaSuccess) return e;
+  e = launch_incident(p->sa, p->omega, p->weight, p->e0, p->eh, p->inc_norm, p->stream);
+  p->z = 0;
+  p->time_valid = false;
+  return e;
+}
+
 }  // namespace
 
 extern "C" {
@@ -265,7 +300,9 @@ BPM_API bpm_status bpm_plan_create(const bpm_grid* grid, int n_channels, void* c
   if (!is_pow2(g.nx) || g.nx < 256 || g.nx > 8192)
     return fail(nullptr, BPM_ERR_UNSUPPORTED, "nx must be a power of two in [256, 8192]");
   const DeviceInfo& di = device_info();
-  if (!di.ok) return fail(nullptr, BPM_ERR_CUDA, "no CUDA device");
+  if (di.cc != 103 && di.sm_count > 0)
+    return fail(nullptr, BPM_ERR_UNSUPPORTED, "libbpm is built for sm_103a (GB300) only");
+  if (!di.ok) return fail(nullptr, BPM_ERR_CUDA, "no usable CUDA device");
   if (di.cc != 103)
     return fail(nullptr, BPM_ERR_UNSUPPORTED, "libbpm is built for sm_103a (GB300) only");
 
@@ -326,6 +363,7 @@ BPM_API bpm_status bpm_plan_create(const bpm_grid* grid, int n_channels, void* c
   p->stats.channels_per_block = p->group;
   p->stats.blocks = p->blocks;
   p->stats.smem_bytes = int(march_smem_bytes(g.nx, p->group));
+  p->bytes = plan_bytes(g, n_channels);
   *out = p.release();
   return BPM_OK;
 }
@@ -364,14 +402,18 @@ BPM_API bpm_status bpm_set_crystal(bpm_plan p, double chi0_re, double chi0_im, d
     if (u_on_device) {
       u_dev = u_field;
     } else {
-      if (!p->u_tmp) BPM_CUDA(p, dalloc(&p->u_tmp, cells), "alloc displacement upload");
+      if (!p->u_tmp) {
+        BPM_CUDA(p, dalloc(&p->u_tmp, cells), "alloc displacement upload");
+        p->bytes += cells * sizeof(double);
+      }
       BPM_CUDA(p, cudaMemcpyAsync(p->u_tmp, u_field, cells * sizeof(double),
                                   cudaMemcpyHostToDevice, p->stream),
                "upload displacement");
       u_dev = p->u_tmp;
     }
   }
-  BPM_CUDA(p, launch_deformation(sa, u_dev, p->cfield, p->stream), "deformation kernel");
+  p->u_dev = u_dev;
+  BPM_CUDA(p, enqueue_crystal(p), "deformation kernel");
   p->have_crystal = true;
   p->have_pulse = false;
   p->time_valid = false;
@@ -386,6 +428,9 @@ BPM_API bpm_status bpm_set_pulse(bpm_plan p, const double* omega, const double* 
   if (!(w0 > 0.0)) return fail(p, BPM_ERR_INVALID_ARG, "w0 must be positive");
   for (int i = 0; i < p->n_ch; ++i)
     if (!(omega[i] > 0.0)) return fail(p, BPM_ERR_INVALID_ARG, "omega must be positive");
+  for (int i = 0; i < p->n_ch; ++i)
+    if (!(omega[i] / 299792458.0 > 0.5 * p->sa.h))
+      return fail(p, BPM_ERR_INVALID_ARG, "a channel has k <= h/2 (no Bragg solution)");
   p->sa.theta_i = theta_i;
   p->sa.x0 = x0;
   p->sa.w0 = w0;
@@ -398,20 +443,8 @@ BPM_API bpm_status bpm_set_pulse(bpm_plan p, const double* omega, const double* 
   BPM_CUDA(p, cudaMemcpyAsync(p->weight, weight_re_im, sizeof(double2) * p->n_ch,
                               cudaMemcpyHostToDevice, p->stream),
            "upload weights");
-  BPM_CUDA(p, cudaMemsetAsync(p->dflag, 0, sizeof(int), p->stream), "clear flag");
-  BPM_CUDA(p, launch_tables(p->sa, p->omega, p->gain, p->rev, p->tables, p->coef, p->dflag,
-                            p->stream),
-           "tables kernel");
-  BPM_CUDA(p, launch_incident(p->sa, p->omega, p->weight, p->e0, p->eh, p->inc_norm, p->stream),
-           "incident kernel");
-  int bad = 0;
-  BPM_CUDA(p, cudaMemcpyAsync(&bad, p->dflag, sizeof(int), cudaMemcpyDeviceToHost, p->stream),
-           "read setup flag");
-  BPM_CUDA(p, cudaStreamSynchronize(p->stream), "pulse setup");
-  if (bad) return fail(p, BPM_ERR_INVALID_ARG, "a channel has k <= h/2 (no Bragg solution)");
-  p->z = 0;
+  BPM_CUDA(p, enqueue_pulse(p), "pulse setup kernels");
   p->have_pulse = true;
-  p->time_valid = false;
   return BPM_OK;
 }
 
@@ -548,6 +581,422 @@ BPM_API void bpm_plan_destroy(bpm_plan p) {
   cudaStreamSynchronize(p->stream);
   free_plan_buffers(p);
   delete p;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Batches: many plans marched by one persistent work-queue launch per round.
+// ===========================================================================
+namespace {
+
+struct BatchEntry {
+  bpm_plan plan = nullptr;
+  uint64_t ticket = 0;
+  bool finishing = false;  // finalize enqueued, done event recorded
+  bool cancelled = false;
+  cudaEvent_t done = nullptr;
+};
+
+// Host staging of one round's descriptors (pinned) and its device copy.
+struct RoundSlot {
+  MarchArgs* h_plans = nullptr;
+  BatchItem* h_items = nullptr;
+  MarchArgs* d_plans = nullptr;
+  BatchItem* d_items = nullptr;
+  int* d_counter = nullptr;  // [2]: small and big queue counters
+  int cap_plans = 0, cap_items = 0;
+  cudaEvent_t free_ev = nullptr;  // recorded after the round's kernels
+  bool used = false;
+};
+
+}  // namespace
+
+struct bpm_batch_s {
+  cudaStream_t stream = nullptr;
+  cudaStream_t side = nullptr;  // Nx = 8192 kernel runs here, forked from stream
+  cudaStream_t cap = nullptr;   // graph capture stream (the caller's may be the legacy stream)
+  cudaEvent_t fork = nullptr, join = nullptr;
+  size_t budget = 0, used = 0;
+  uint64_t next_ticket = 1;
+  std::vector<BatchEntry> entries;
+  std::map<uint64_t, int> finished;  // ticket -> 1 done, 2 cancelled
+  RoundSlot slots[3];
+  int next_slot = 0;
+  RoundSlot graph_slot;
+  cudaGraphExec_t graph = nullptr;
+  uint64_t graph_key = 0;
+  std::string err = "no error";
+  int rounds = 0;
+  int last_items[2] = {0, 0};
+};
+
+namespace {
+
+bpm_status bfail(bpm_batch b, bpm_status s, const std::string& msg) {
+  if (b) b->err = msg;
+  g_thread_error = msg;
+  return s;
+}
+
+#define BPM_BCUDA(b, call, what)                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return bfail((b), e_ == cudaErrorMemoryAllocation ? BPM_ERR_OOM : BPM_ERR_CUDA, \
+                   std::string(what) + ": " + cudaGetErrorString(e_));                 \
+  } while (0)
+
+cudaError_t slot_reserve(RoundSlot& r, int n_plans, int n_items) {
+  cudaError_t e = cudaSuccess;
+  if (n_plans > r.cap_plans) {
+    if (r.h_plans) cudaFreeHost(r.h_plans);
+    if (r.d_plans) cudaFree(r.d_plans);
+    r.cap_plans = n_plans * 2;
+    if ((e = cudaMallocHost(&r.h_plans, sizeof(MarchArgs) * r.cap_plans)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&r.d_plans, sizeof(MarchArgs) * r.cap_plans)) != cudaSuccess) return e;
+  }
+  if (n_items > r.cap_items) {
+    if (r.h_items) cudaFreeHost(r.h_items);
+    if (r.d_items) cudaFree(r.d_items);
+    r.cap_items = n_items * 2;
+    if ((e = cudaMallocHost(&r.h_items, sizeof(BatchItem) * r.cap_items)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&r.d_items, sizeof(BatchItem) * r.cap_items)) != cudaSuccess) return e;
+  }
+  if (!r.d_counter && (e = cudaMalloc(&r.d_counter, 2 * sizeof(int))) != cudaSuccess) return e;
+  if (!r.free_ev && (e = cudaEventCreateWithFlags(&r.free_ev, cudaEventDisableTiming)) != cudaSuccess)
+    return e;
+  return cudaSuccess;
+}
+
+void slot_free(RoundSlot& r) {
+  if (r.h_plans) cudaFreeHost(r.h_plans);
+  if (r.h_items) cudaFreeHost(r.h_items);
+  if (r.d_plans) cudaFree(r.d_plans);
+  if (r.d_items) cudaFree(r.d_items);
+  if (r.d_counter) cudaFree(r.d_counter);
+  if (r.free_ev) cudaEventDestroy(r.free_ev);
+  r = RoundSlot();
+}
+
+MarchArgs march_args(bpm_plan p, int n_steps) {
+  MarchArgs a;
+  a.tables = p->tables;
+  a.coef = p->coef;
+  a.twiddle = p->twiddle;
+  a.cfield = p->cfield;
+  a.e0 = p->e0;
+  a.eh = p->eh;
+  a.inc_norm = p->inc_norm;
+  a.refl = p->refl;
+  a.trans = p->trans;
+  a.n_ch = p->n_ch;
+  a.z0 = p->z;
+  a.n_steps = n_steps;
+  return a;
+}
+
+// Enqueue one round on b->stream using slot r: every active entry advances
+// min(chunk, nz - z) steps; entries that reach nz get their time response and
+// a completion event.  Items are ordered longest-first within each queue.
+bpm_status enqueue_round(bpm_batch b, RoundSlot& r, int chunk) {
+  std::vector<int> act;
+  for (int i = 0; i < int(b->entries.size()); ++i) {
+    const BatchEntry& e = b->entries[i];
+    if (!e.finishing && !e.cancelled && e.plan->z < e.plan->grid.nz) act.push_back(i);
+  }
+  if (act.empty()) return BPM_OK;
+  struct Tmp {
+    BatchItem it;
+    double cost;
+    bool big;
+  };
+  std::vector<Tmp> tmp;
+  std::vector<int> steps(act.size());
+  for (int k = 0; k < int(act.size()); ++k) {
+    bpm_plan p = b->entries[act[k]].plan;
+    const int n = p->grid.nx;
+    steps[k] = std::min(chunk, p->grid.nz - p->z);
+    const int G = batch_group(n);
+    for (int c0 = 0; c0 < p->n_ch; c0 += G) {
+      Tmp t;
+      t.it = BatchItem{k, c0, n, 0};
+      t.cost = double(steps[k]) * n * std::min(G, p->n_ch - c0) * std::log2(double(n));
+      t.big = (n == 8192);
+      tmp.push_back(t);
+    }
+  }
+  std::stable_sort(tmp.begin(), tmp.end(), [](const Tmp& x, const Tmp& y) { return x.cost > y.cost; });
+  int n_small = 0, n_big = 0;
+  for (auto& t : tmp) (t.big ? n_big : n_small)++;
+  BPM_BCUDA(b, slot_reserve(r, int(act.size()), int(tmp.size())), "batch staging");
+  if (r.used) BPM_BCUDA(b, cudaEventSynchronize(r.free_ev), "staging reuse");
+  for (int k = 0; k < int(act.size()); ++k) r.h_plans[k] = march_args(b->entries[act[k]].plan, steps[k]);
+  int is = 0, ib = n_small;
+  for (auto& t : tmp) r.h_items[t.big ? ib++ : is++] = t.it;
+  const DeviceInfo& di = device_info();
+  BPM_BCUDA(b, cudaMemcpyAsync(r.d_plans, r.h_plans, sizeof(MarchArgs) * act.size(),
+                               cudaMemcpyHostToDevice, b->stream), "upload round");
+  BPM_BCUDA(b, cudaMemcpyAsync(r.d_items, r.h_items, sizeof(BatchItem) * tmp.size(),
+                               cudaMemcpyHostToDevice, b->stream), "upload items");
+  BPM_BCUDA(b, cudaMemsetAsync(r.d_counter, 0, 2 * sizeof(int), b->stream), "clear queue");
+  // split the SMs between the two queues in proportion to their work so that
+  // both drain together (one block per SM for either kernel)
+  double w_small = 0.0, w_big = 0.0;
+  for (auto& t : tmp) (t.big ? w_big : w_small) += t.cost;
+  int big_blocks = 0, small_blocks = 0;
+  if (n_big > 0 && n_small > 0) {
+    big_blocks = int(std::lround(di.sm_count * w_big / (w_big + w_small)));
+    big_blocks = std::max(1, std::min(big_blocks, di.sm_count - 1));
+    small_blocks = di.sm_count - big_blocks;
+  } else {
+    big_blocks = di.sm_count;
+    small_blocks = di.sm_count;
+  }
+  big_blocks = std::min(big_blocks, n_big);
+  small_blocks = std::min(small_blocks, n_small);
+  if (n_big > 0) {
+    BPM_BCUDA(b, cudaEventRecord(b->fork, b->stream), "fork");
+    BPM_BCUDA(b, cudaStreamWaitEvent(b->side, b->fork, 0), "fork wait");
+    BPM_BCUDA(b, launch_batch(r.d_plans, r.d_items + n_small, n_big, r.d_counter + 1, true,
+                              big_blocks, b->side),
+              "batch kernel (Nx 8192)");
+    BPM_BCUDA(b, cudaEventRecord(b->join, b->side), "join");
+  }
+  if (n_small > 0)
+    BPM_BCUDA(b, launch_batch(r.d_plans, r.d_items, n_small, r.d_counter, false, small_blocks,
+                              b->stream),
+              "batch kernel");
+  if (n_big > 0) BPM_BCUDA(b, cudaStreamWaitEvent(b->stream, b->join, 0), "join wait");
+  BPM_BCUDA(b, cudaEventRecord(r.free_ev, b->stream), "round event");
+  r.used = true;
+  b->last_items[0] = n_small;
+  b->last_items[1] = n_big;
+  ++b->rounds;
+  for (int k = 0; k < int(act.size()); ++k) {
+    BatchEntry& e = b->entries[act[k]];
+    bpm_plan p = e.plan;
+    p->z += steps[k];
+    p->time_valid = false;
+    if (p->z == p->grid.nz) {
+      BPM_BCUDA(b, launch_omega_to_t(p->n_ch, p->plane, p->domega, p->eh, p->eh_time, b->stream),
+                "omega-to-t kernel");
+      p->time_valid = true;
+      if (!e.done) BPM_BCUDA(b, cudaEventCreateWithFlags(&e.done, cudaEventDisableTiming), "event");
+      BPM_BCUDA(b, cudaEventRecord(e.done, b->stream), "completion event");
+      e.finishing = true;
+    }
+  }
+  return BPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+BPM_API size_t bpm_plan_bytes(const bpm_grid* grid, int n_channels, int host_u) {
+  if (!grid || n_channels < 1) return 0;
+  size_t b = plan_bytes(*grid, n_channels);
+  if (host_u) b += size_t(grid->nz) * grid->nx * (grid->dims == 3 ? grid->ny : 1) * sizeof(double);
+  return b;
+}
+
+BPM_API bpm_status bpm_batch_create(size_t hbm_budget_bytes, void* cuda_stream, bpm_batch* out) {
+  if (!out) return bfail(nullptr, BPM_ERR_INVALID_ARG, "null output");
+  *out = nullptr;
+  const DeviceInfo& di = device_info();
+  if (!di.ok || di.cc != 103)
+    return bfail(nullptr, BPM_ERR_UNSUPPORTED, "libbpm needs a GB300 (sm_103a) device");
+  auto b = std::make_unique<bpm_batch_s>();
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  b->budget = hbm_budget_bytes;
+  BPM_BCUDA(b.get(), cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking), "side stream");
+  BPM_BCUDA(b.get(), cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "capture stream");
+  BPM_BCUDA(b.get(), cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "event");
+  BPM_BCUDA(b.get(), cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming), "event");
+  *out = b.release();
+  return BPM_OK;
+}
+
+BPM_API bpm_status bpm_batch_submit(bpm_batch b, bpm_plan p, uint64_t* ticket) {
+  if (!b || !p || !ticket) return bfail(b, BPM_ERR_INVALID_ARG, "null argument");
+  if (!p->have_pulse) return bfail(b, BPM_ERR_STATE, "plan needs crystal and pulse first");
+  if (p->grid.dims != 2) return bfail(b, BPM_ERR_UNSUPPORTED, "batches take 2D plans");
+  for (const auto& e : b->entries)
+    if (e.plan == p) return bfail(b, BPM_ERR_STATE, "plan already in the batch");
+  if (b->budget && b->used + p->bytes > b->budget)
+    return bfail(b, BPM_ERR_OOM, "not admitted: HBM budget exhausted");
+  if (p->stream != b->stream) {
+    // order the plan's setup work before the batch's rounds, then adopt the batch stream
+    cudaEvent_t ev;
+    BPM_BCUDA(b, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+    BPM_BCUDA(b, cudaEventRecord(ev, p->stream), "event");
+    BPM_BCUDA(b, cudaStreamWaitEvent(b->stream, ev, 0), "event wait");
+    cudaEventDestroy(ev);
+    p->stream = b->stream;
+  }
+  BatchEntry e;
+  e.plan = p;
+  e.ticket = b->next_ticket++;
+  b->entries.push_back(e);
+  b->used += p->bytes;
+  *ticket = e.ticket;
+  return BPM_OK;
+}
+
+BPM_API bpm_status bpm_batch_step(bpm_batch b, int chunk_steps) {
+  if (!b) return bfail(nullptr, BPM_ERR_INVALID_ARG, "null batch");
+  if (chunk_steps < 1) return bfail(b, BPM_ERR_INVALID_ARG, "chunk_steps must be >= 1");
+  RoundSlot& r = b->slots[b->next_slot];
+  b->next_slot = (b->next_slot + 1) % 3;
+  return enqueue_round(b, r, chunk_steps);
+}
+
+BPM_API bpm_status bpm_batch_run(bpm_batch b) { return bpm_batch_step(b, 1 << 30); }
+
+BPM_API bpm_status bpm_batch_poll(bpm_batch b, uint64_t ticket, int* done) {
+  if (!b || !done) return bfail(b, BPM_ERR_INVALID_ARG, "null argument");
+  *done = 0;
+  auto f = b->finished.find(ticket);
+  if (f != b->finished.end()) {
+    if (f->second == 2) return bfail(b, BPM_ERR_CANCELLED, "ticket was cancelled");
+    *done = 1;
+    return BPM_OK;
+  }
+  for (size_t i = 0; i < b->entries.size(); ++i) {
+    BatchEntry& e = b->entries[i];
+    if (e.ticket != ticket) continue;
+    if (!e.finishing) return BPM_OK;
+    cudaError_t q = cudaEventQuery(e.done);
+    if (q == cudaErrorNotReady) return BPM_OK;
+    if (q != cudaSuccess) return bfail(b, BPM_ERR_CUDA, cudaGetErrorString(q));
+    cudaEventDestroy(e.done);
+    b->used -= e.plan->bytes;
+    b->finished[ticket] = 1;
+    b->entries.erase(b->entries.begin() + long(i));
+    *done = 1;
+    return BPM_OK;
+  }
+  return bfail(b, BPM_ERR_INVALID_ARG, "unknown ticket");
+}
+
+BPM_API bpm_status bpm_batch_cancel(bpm_batch b, uint64_t ticket) {
+  if (!b) return bfail(nullptr, BPM_ERR_INVALID_ARG, "null batch");
+  for (size_t i = 0; i < b->entries.size(); ++i) {
+    BatchEntry& e = b->entries[i];
+    if (e.ticket != ticket) continue;
+    if (e.finishing) return bfail(b, BPM_ERR_STATE, "ticket already finishing");
+    // rounds already enqueued may still touch the plan: wait for them
+    BPM_BCUDA(b, cudaStreamSynchronize(b->stream), "cancel");
+    b->used -= e.plan->bytes;
+    b->finished[ticket] = 2;
+    b->entries.erase(b->entries.begin() + long(i));
+    return BPM_OK;
+  }
+  return bfail(b, BPM_ERR_INVALID_ARG, "unknown or finished ticket");
+}
+
+BPM_API bpm_status bpm_batch_sync(bpm_batch b) {
+  if (!b) return bfail(nullptr, BPM_ERR_INVALID_ARG, "null batch");
+  BPM_BCUDA(b, cudaStreamSynchronize(b->stream), "batch synchronize");
+  return BPM_OK;
+}
+
+// Replays, as one CUDA graph, the whole hot path of every entry in the batch:
+// deformation factor, tables and incident field from the stored inputs, one
+// round to nz, time response.  The graph is captured on the first call and
+// again whenever the set of entries changes.
+BPM_API bpm_status bpm_batch_run_graph(bpm_batch b) {
+  if (!b) return bfail(nullptr, BPM_ERR_INVALID_ARG, "null batch");
+  uint64_t key = 1469598103934665603ull;
+  for (const auto& e : b->entries) key = (key ^ reinterpret_cast<uintptr_t>(e.plan)) * 1099511628211ull;
+  if (!b->graph || key != b->graph_key) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    BPM_BCUDA(b, cudaStreamSynchronize(b->stream), "pre-capture sync");
+    // allocations happen before the capture: staging for every item, completion events
+    int n_items = 0;
+    for (auto& e : b->entries) {
+      const int G = batch_group(e.plan->grid.nx);
+      n_items += (e.plan->n_ch + G - 1) / G;
+      if (!e.done) BPM_BCUDA(b, cudaEventCreateWithFlags(&e.done, cudaEventDisableTiming), "event");
+    }
+    BPM_BCUDA(b, slot_reserve(b->graph_slot, int(b->entries.size()), n_items), "graph staging");
+    // capture on the batch's own stream; the graph is launched on the caller's
+    cudaStream_t user = b->stream;
+    b->stream = b->cap;
+    for (auto& e : b->entries) {
+      e.finishing = false;
+      e.plan->z = 0;
+      e.plan->stream = b->cap;
+    }
+    bpm_status st = BPM_OK;
+    cudaGraph_t g = nullptr;
+    cudaError_t be = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (be != cudaSuccess) {
+      st = bfail(b, BPM_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(be));
+    } else {
+      for (auto& e : b->entries) {
+        if (enqueue_crystal(e.plan) != cudaSuccess || enqueue_pulse(e.plan) != cudaSuccess) {
+          st = bfail(b, BPM_ERR_CUDA, "setup launch during capture");
+          break;
+        }
+      }
+      if (st == BPM_OK) st = enqueue_round(b, b->graph_slot, 1 << 30);
+    }
+    cudaError_t ce = be == cudaSuccess ? cudaStreamEndCapture(b->cap, &g) : cudaSuccess;
+    b->stream = user;
+    for (auto& e : b->entries) e.plan->stream = user;
+    if (st != BPM_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    BPM_BCUDA(b, ce, "end capture");
+    cudaError_t ie = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    BPM_BCUDA(b, ie, "graph instantiate");
+    b->graph_key = key;
+    b->graph_slot.used = false;  // the captured round has not run yet
+  }
+  for (auto& e : b->entries) {
+    e.plan->z = e.plan->grid.nz;
+    e.plan->time_valid = true;
+  }
+  BPM_BCUDA(b, cudaGraphLaunch(b->graph, b->stream), "graph launch");
+  return BPM_OK;
+}
+
+BPM_API bpm_status bpm_batch_info(bpm_batch b, int* active, size_t* used_bytes, int* rounds,
+                                  int* last_items) {
+  if (!b) return bfail(nullptr, BPM_ERR_INVALID_ARG, "null batch");
+  if (active) *active = int(b->entries.size());
+  if (used_bytes) *used_bytes = b->used;
+  if (rounds) *rounds = b->rounds;
+  if (last_items) {
+    last_items[0] = b->last_items[0];
+    last_items[1] = b->last_items[1];
+  }
+  return BPM_OK;
+}
+
+BPM_API const char* bpm_batch_last_error(bpm_batch b) {
+  return b ? b->err.c_str() : g_thread_error.c_str();
+}
+
+BPM_API void bpm_batch_destroy(bpm_batch b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  if (b->side) cudaStreamSynchronize(b->side);
+  for (auto& e : b->entries)
+    if (e.done) cudaEventDestroy(e.done);
+  for (auto& r : b->slots) slot_free(r);
+  slot_free(b->graph_slot);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->join) cudaEventDestroy(b->join);
+  if (b->side) cudaStreamDestroy(b->side);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
 }
 
 }  // extern "C"

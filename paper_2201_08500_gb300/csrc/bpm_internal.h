@@ -46,6 +46,25 @@ struct SetupArgs {
   double theta_i, x0, w0, zx, zR;
 };
 
+// One work-queue item: channels ch0 .. ch0 + G - 1 of plan `plan` (transform size n).
+struct BatchItem {
+  int plan;
+  int ch0;
+  int n;
+  int reserved;
+};
+
+// Work-queue launchers (bpm_batch.cu).  big selects the Nx = 8192 kernel.
+int batch_group(int n);
+cudaError_t launch_batch(const MarchArgs* plans, const BatchItem* items, int n_items, int* counter,
+                         bool big, int blocks, cudaStream_t s);
+
+// One-time kernel attribute setup (dynamic shared memory limits); must run
+// outside stream capture, before the first launch on the current device.
+cudaError_t march_set_attributes();
+cudaError_t batch_set_attributes();
+cudaError_t setup_set_attributes();
+
 // Launchers (bpm_march.cu).  Return cudaSuccess or the launch error.
 int march_threads_per_channel(int n);
 int march_max_group(int n);

@@ -214,7 +214,7 @@ __global__ void omega_to_t_fft_kernel(int n, int logn, long long plane, double d
   const int cols = int(min((long long)kCols, plane - x0));
   for (int idx = threadIdx.x; idx < n * kCols; idx += blockDim.x) {
     const int i = idx / kCols, c = idx % kCols;
-    const int ri = int(__brev(unsigned(i)) >> (32 - logn));
+    const int ri = logn ? int(__brev(unsigned(i)) >> (32 - logn)) : 0;
     double2 v = make_double2(0.0, 0.0);
     if (c < cols) {
       const float2 f = eh[(long long)i * plane + x0 + c];
@@ -272,6 +272,11 @@ __global__ void omega_to_t_direct_kernel(int n, long long plane, double domega,
 
 }  // namespace
 
+cudaError_t setup_set_attributes() {
+  return cudaFuncSetAttribute(omega_to_t_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              200 * 1024);
+}
+
 cudaError_t launch_deformation(const SetupArgs& sa, const double* u_dev, float2* cfield,
                                cudaStream_t s) {
   const long long total = (long long)sa.nx * sa.ny * sa.nz;
@@ -301,9 +306,6 @@ cudaError_t launch_omega_to_t(int n_ch, long long plane, double domega, const fl
   if (pow2 && smem <= 200 * 1024) {
     int logn = 0;
     while ((1 << logn) < n_ch) ++logn;
-    cudaError_t e = cudaFuncSetAttribute(omega_to_t_fft_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
     const long long blocks = (plane + kCols - 1) / kCols;
     omega_to_t_fft_kernel<<<int(blocks), 256, smem, s>>>(n_ch, logn, plane, domega, eh, out);
     return cudaGetLastError();

@@ -145,7 +145,7 @@ def _strain_field(kind, rng, nx, nz, dx, dz, xs, d):
         R = rng.uniform(1.0, 50.0)
         u = np.broadcast_to(-((z - Z / 2) ** 2) / (2.0 * R), (nx, nz)).T.copy()
         return u, dict(R=R)
-    # random smooth strain: sum of 8 Gaussians in (depth, z)
+    # random smooth strain: sum of 8 Gaussians in (depth, z), each separable
     xp = x - xs
     u = np.zeros((nz, nx))
     L = nx * dx
@@ -155,7 +155,7 @@ def _strain_field(kind, rng, nx, nz, dx, dz, xs, d):
         cz = rng.uniform(0.0, Z)
         wx = rng.uniform(L / 32, L / 4)
         wz = rng.uniform(L / 32, L / 4)
-        u += a * np.exp(-((xp[None, :] - cx) ** 2) / wx ** 2 - ((z[:, None] - cz) ** 2) / wz ** 2)
+        u += a * np.outer(np.exp(-((z - cz) ** 2) / wz ** 2), np.exp(-((xp - cx) ** 2) / wx ** 2))
     return u, {}
 
 

@@ -239,6 +239,59 @@ BPM_API const char* bpm_batch_last_error(bpm_batch b);
 /* Waits for the batch stream and frees the batch (not the plans). */
 BPM_API void bpm_batch_destroy(bpm_batch b);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free single-instance run.  The paper has no counterpart: this is
+ * a deployment convenience of this library.
+ *
+ * For callers that cannot allocate device memory while they run this code:
+ * work being recorded into a CUDA graph (cudaMalloc is not a stream operation
+ * and cannot be captured), processes whose device memory is wholly handed out
+ * by their own pool, and latency-bound loops that must not take the
+ * allocator's lock.  The caller passes the inputs and outputs; every
+ * intermediate buffer (deformation factor, propagator tables, coupling
+ * coefficients, FFT constants, norms) lives in one fixed device array inside
+ * the library (bpm_noalloc_scratch_bytes(), 6.3 MB), which every GPU that
+ * loads the library holds until the process exits.  No call here allocates or
+ * frees device or pinned memory.
+ *
+ * Limits (anything larger returns BPM_ERR_UNSUPPORTED and a message in
+ * bpm_noalloc_last_error): dims = 2, nx a power of two in [256, 4096],
+ * n_channels <= 16, nz * nx <= 524288 cells.
+ *
+ * Results equal those of a plan created with the same inputs followed by
+ * bpm_run(nz): E0 and Eh at z = nz into e0_dev / eh_dev (device complex64
+ * [n_channels][nx]), reflectivities R_i into refl_dev (device float64
+ * [n_channels]).  u_field_dev is a device float64 [nz][nx] displacement or
+ * NULL (perfect crystal); omega and weight_re_im are host arrays as for
+ * bpm_set_pulse.  Asynchronous on cuda_stream.
+ *
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All calls
+ * share the one array and it keeps the last call's contents: two calls whose
+ * work overlaps on the GPU (different streams, or different host threads)
+ * race and corrupt each other, so serialise them on one stream.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  double chi0_re, chi0_im, chih_re, chih_im, chihbar_re, chihbar_im;
+  double theta_B, lambda_B, x_surface, thickness;
+} bpm_crystal_params;
+
+typedef struct {
+  double theta_i, x0, w0, zx, zR;
+} bpm_beam_params;
+
+BPM_API bpm_status bpm_run_noalloc(const bpm_grid* grid, int n_channels,
+                                   const bpm_crystal_params* crystal, const double* u_field_dev,
+                                   const double* omega, const double* weight_re_im,
+                                   const bpm_beam_params* beam, void* e0_dev, void* eh_dev,
+                                   double* refl_dev, void* cuda_stream);
+
+/* Size in bytes of the fixed device array used by bpm_run_noalloc. */
+BPM_API size_t bpm_noalloc_scratch_bytes(void);
+
+/* Message of the last failed bpm_run_noalloc call of this thread. */
+BPM_API const char* bpm_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

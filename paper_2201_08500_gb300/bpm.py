@@ -25,7 +25,8 @@ EXPORTS = ("bpm_plan_create", "bpm_set_crystal", "bpm_set_pulse", "bpm_set_field
            "bpm_get_stats", "bpm_last_error", "bpm_plan_destroy", "bpm_version", "bpm_plan_bytes",
            "bpm_batch_create", "bpm_batch_submit", "bpm_batch_step", "bpm_batch_run",
            "bpm_batch_run_graph", "bpm_batch_poll", "bpm_batch_cancel", "bpm_batch_sync",
-           "bpm_batch_info", "bpm_batch_last_error", "bpm_batch_destroy")
+           "bpm_batch_info", "bpm_batch_last_error", "bpm_batch_destroy", "bpm_run_noalloc",
+           "bpm_noalloc_scratch_bytes", "bpm_noalloc_last_error")
 
 
 class BpmError(RuntimeError):
@@ -46,6 +47,16 @@ class Stats(ctypes.Structure):
                 ("march_launches", ctypes.c_int32), ("threads_per_channel", ctypes.c_int32),
                 ("channels_per_block", ctypes.c_int32), ("blocks", ctypes.c_int32),
                 ("smem_bytes", ctypes.c_int32)]
+
+
+class CrystalParams(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("chi0_re", "chi0_im", "chih_re", "chih_im",
+                                               "chihbar_re", "chihbar_im", "theta_B", "lambda_B",
+                                               "x_surface", "thickness")]
+
+
+class BeamParams(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("theta_i", "x0", "w0", "zx", "zR")]
 
 
 _lib = None
@@ -90,6 +101,10 @@ def load(path: str = LIB_PATH):
                             ctypes.POINTER(_I), ctypes.POINTER(_I * 2)], _I),
         "bpm_batch_last_error": ([_P], ctypes.c_char_p),
         "bpm_batch_destroy": ([_P], None),
+        "bpm_run_noalloc": ([ctypes.POINTER(Grid), _I, ctypes.POINTER(CrystalParams), _P, _P, _P,
+                             ctypes.POINTER(BeamParams), _P, _P, _P, _P], _I),
+        "bpm_noalloc_scratch_bytes": ([], ctypes.c_size_t),
+        "bpm_noalloc_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -325,3 +340,24 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def run_noalloc(w, e0_out, eh_out, refl_out, u_dev=None, stream=None):
+    """Allocation-free single-instance run (bpm_run_noalloc) of a workload record.
+
+    e0_out, eh_out: device complex64 [n_ch, nx]; refl_out: device float64 [n_ch];
+    u_dev: device float64 [nz, nx] displacement or None.  For callers that must
+    not allocate device memory while they run (see include/bpm.h)."""
+    L = load()
+    g = Grid(2, int(w.nx), 1, int(w.nz), float(w.dx), 0.0, float(w.dz), 1, int(w.zassenhaus))
+    chi0, chih, chihb = complex(w.chi0), complex(w.chih), complex(w.chihb)
+    c = CrystalParams(chi0.real, chi0.imag, chih.real, chih.imag, chihb.real, chihb.imag,
+                      float(w.theta_B), float(w.lambda_B), float(w.x_surface), float(w.thickness))
+    b = BeamParams(float(w.theta_i), float(w.x0), float(w.w0), float(w.zx), float(w.zR))
+    omega = np.ascontiguousarray(w.omega, dtype=np.float64)
+    S = np.ascontiguousarray(w.S, dtype=np.complex128)
+    st = L.bpm_run_noalloc(ctypes.byref(g), int(w.n_ch), ctypes.byref(c), _ptr(u_dev),
+                           _ptr(omega), _ptr(S), ctypes.byref(b), _ptr(e0_out), _ptr(eh_out),
+                           _ptr(refl_out), _stream_handle(stream))
+    if st != 0:
+        raise BpmError(st, L.bpm_noalloc_last_error().decode())

@@ -164,6 +164,20 @@ const DeviceInfo& device_info() {
 
 }  // namespace
 
+namespace bpm {
+void fft_host_constants(int n, const float2** tw, const int** rev, const double** gain) {
+  const FftConsts& f = fft_consts(n);
+  *tw = f.tw.data();
+  *rev = f.rev.data();
+  *gain = f.gain.data();
+}
+bool device_ready(int* sm_count) {
+  const DeviceInfo& d = device_info();
+  if (sm_count) *sm_count = d.sm_count;
+  return d.ok && d.cc == 103;
+}
+}  // namespace bpm
+
 struct bpm_plan_s {
   bpm_grid grid{};
   int n_ch = 0;

@@ -59,6 +59,12 @@ int batch_group(int n);
 cudaError_t launch_batch(const MarchArgs* plans, const BatchItem* items, int n_items, int* counter,
                          bool big, int blocks, cudaStream_t s);
 
+// Host runtime helpers (bpm_api.cu): FFT constants of size n (twiddles, spectrum
+// order, round-trip gain; host memory owned by a process-wide cache) and a
+// readiness check of the current device (sm_103, kernel attributes set).
+void fft_host_constants(int n, const float2** tw, const int** rev, const double** gain);
+bool device_ready(int* sm_count);
+
 // One-time kernel attribute setup (dynamic shared memory limits); must run
 // outside stream capture, before the first launch on the current device.
 cudaError_t march_set_attributes();

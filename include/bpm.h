@@ -119,6 +119,12 @@ BPM_API bpm_status bpm_set_fields(bpm_plan plan, const void* e0, const void* eh,
  * Errors: INVALID_ARG (n_steps < 0 or past nz), STATE (no pulse), CUDA. */
 BPM_API bpm_status bpm_run(bpm_plan plan, int n_steps);
 
+/* Moves the plan to another stream (a cudaStream_t; NULL = legacy stream): work
+ * enqueued later by this plan goes there, ordered after everything already
+ * enqueued on the old stream.  Used to reuse pooled plans: set up and fetch on a
+ * setup stream while a batch stream keeps marching others.  Errors: CUDA. */
+BPM_API bpm_status bpm_set_stream(bpm_plan plan, void* cuda_stream);
+
 /* Waits for the plan's stream and reports device status: TIMEOUT if a bounded
  * device wait gave up, CUDA on an asynchronous error. */
 BPM_API bpm_status bpm_sync(bpm_plan plan);
@@ -190,8 +196,9 @@ typedef struct bpm_batch_s* bpm_batch;
 BPM_API bpm_status bpm_batch_create(size_t hbm_budget_bytes, void* cuda_stream, bpm_batch* out);
 
 /* Admits a plan whose crystal and pulse are set; it is marched from its current
- * z to nz by later rounds.  The plan's stream is replaced by the batch stream
- * (its pending work is ordered before the batch).  The caller keeps ownership
+ * z to nz by later rounds.  Until its ticket completes (or is cancelled) the
+ * plan works on the batch stream (its pending work is ordered before the
+ * batch); then its original stream is restored.  The caller keeps ownership
  * and destroys the plan after its ticket reports done (or after cancel).
  * Errors: OOM (budget exhausted: not admitted, retry later), STATE (no pulse,
  * already admitted), UNSUPPORTED (3D plan), INVALID_ARG. */

@@ -26,7 +26,7 @@ EXPORTS = ("bpm_plan_create", "bpm_set_crystal", "bpm_set_pulse", "bpm_set_field
            "bpm_batch_create", "bpm_batch_submit", "bpm_batch_step", "bpm_batch_run",
            "bpm_batch_run_graph", "bpm_batch_poll", "bpm_batch_cancel", "bpm_batch_sync",
            "bpm_batch_info", "bpm_batch_last_error", "bpm_batch_destroy", "bpm_run_noalloc",
-           "bpm_noalloc_scratch_bytes", "bpm_noalloc_last_error")
+           "bpm_noalloc_scratch_bytes", "bpm_noalloc_last_error", "bpm_set_stream")
 
 
 class BpmError(RuntimeError):
@@ -81,6 +81,7 @@ def load(path: str = LIB_PATH):
         "bpm_set_fields": ([_P, _P, _P, _I, _I], _I),
         "bpm_run": ([_P, _I], _I),
         "bpm_sync": ([_P], _I),
+        "bpm_set_stream": ([_P, _P], _I),
         "bpm_fetch_fields": ([_P, _I, _P, ctypes.c_size_t, _I], _I),
         "bpm_fetch_reflectivity": ([_P, _P, _P, _P], _I),
         "bpm_set_timing": ([_P, _I], _I),
@@ -216,6 +217,9 @@ class Plan:
 
     def sync(self):
         self._check(self._L.bpm_sync(self._h))
+
+    def set_stream(self, stream):
+        self._check(self._L.bpm_set_stream(self._h, _stream_handle(stream)))
 
     def fetch(self, which: int, out=None):
         shape = (self.n_channels, self.plane)

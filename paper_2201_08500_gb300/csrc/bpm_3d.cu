@@ -1,0 +1,396 @@
+// 3D (x, y, z) form of the two-beam BPM: the transverse field of one channel
+// (Nx x Ny complex64 per envelope) does not fit on chip, so every z step
+// streams both envelopes through HBM in two passes (Eq. fov4 with the 2D
+// transverse Laplacian, Eq. fov10 coupling):
+//
+//   column pass : for a tile of W x-frequency columns, staged through padded
+//                 shared memory: forward y-FFT, multiply by the tilted
+//                 propagator p+-(qx, qy), inverse y-FFT, write back;
+//   row pass    : per row y: inverse x-FFT, pointwise coupling with
+//                 c(x, y, z_n) = Pi(x) exp(+i h u(x, y, z_n)), then the next
+//                 step's forward x-FFT, write back.
+//
+// Between passes the fields are stored as [ch][y][sigma(px)]: the x-spectrum in
+// the FFT's digit-reversed positions px, permuted by sigma(px) = (px % 16) T +
+// px / 16 (T = Nx / 16) so that the row FFT's register layout (thread t holds
+// px = 16 t + k) loads and stores coalesced.  A run of n steps is: one row pass
+// (forward x of the x-space fields), then n x (column pass, row pass); the
+// last row pass leaves natural x order.  Traffic: 2 passes x 2 envelopes x
+// (8 B read + 8 B write) = 64 B per cell-update.
+//
+// Propagator: p(qx, qy) = exp(i dz [sqrt(K^2 - qy^2) - k]), K^2 = k^2 - (qx +- h/2)^2,
+// written as an FP64 anchor exp(i dz [K - k]) per column (FP32 hi + lo, with
+// 1/(Nx Ny) and the x round-trip gain folded in) times
+// 1 + i c - c^2/2 - delta_y, where c = -dz qy^2 / (2K) (|c| < 1e-4 here, so the
+// dropped terms are below 1e-12) and delta_y removes the y round-trip gain.
+#include <cuda_runtime.h>
+
+#include "bpm_fft.cuh"
+#include "bpm_internal.h"
+
+namespace bpm {
+namespace {
+
+// Synchronisation of one transform group of T threads (g = group index in the block).
+template <int T>
+BPM_DEV void g3_sync(int g) {
+  if constexpr (T == 16) {
+    __syncwarp((threadIdx.x & 16u) ? 0xFFFF0000u : 0x0000FFFFu);
+  } else if constexpr (T == 32) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(T) : "memory");
+  }
+}
+
+// Paired (E0, Eh) transform of size N held by a group of T = N/16 threads, 16
+// values per thread and envelope.  `buf` is the group's exchange area: element p
+// of envelope e lives at buf[(swz(p) * stride) + e * estride].
+template <int N>
+struct Fft2Env {
+  using Gm = Geom<N>;
+  static constexpr int T = Gm::T;
+  static constexpr int S = Gm::S;
+
+  template <int s>
+  static BPM_DEV void twid(float2 (&a)[16], float2 (&b)[16], const float2* tw, int t, bool inv) {
+    constexpr int ln = Gm::LN(s);
+    constexpr int stride = N / Gm::L(s);
+    const int j = t % ln;
+#pragma unroll
+    for (int m = 1; m < 16; ++m) {
+      const float2 w = __ldg(tw + stride * j * m);
+      a[m] = inv ? c_mulc(a[m], w) : c_mul(a[m], w);
+      b[m] = inv ? c_mulc(b[m], w) : c_mul(b[m], w);
+    }
+  }
+
+  template <int SF, int ST>
+  static BPM_DEV void xchg(float2 (&a)[16], float2 (&b)[16], float2* buf, int stride, int estride,
+                           int t, int g) {
+    g3_sync<T>(g);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int p = swz(Gm::template pos<SF>(t, k)) * stride;
+      buf[p] = a[k];
+      buf[p + estride] = b[k];
+    }
+    g3_sync<T>(g);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int p = swz(Gm::template pos<ST>(t, k)) * stride;
+      a[k] = buf[p];
+      b[k] = buf[p + estride];
+    }
+  }
+
+  template <int s>
+  static BPM_DEV void sfwd(float2 (&a)[16], float2 (&b)[16], const float2* tw, int t) {
+    if constexpr (s < S - 1) {
+      dft16_fwd(a);
+      dft16_fwd(b);
+      twid<s>(a, b, tw, t, false);
+    } else {
+      last_stage<Gm::RLAST, false>(a);
+      last_stage<Gm::RLAST, false>(b);
+    }
+  }
+
+  template <int s>
+  static BPM_DEV void sinv(float2 (&a)[16], float2 (&b)[16], const float2* tw, int t) {
+    if constexpr (s < S - 1) {
+      twid<s>(a, b, tw, t, true);
+      dft16_inv(a);
+      dft16_inv(b);
+    } else {
+      last_stage<Gm::RLAST, true>(a);
+      last_stage<Gm::RLAST, true>(b);
+    }
+  }
+
+  // natural layout (pos<0>) -> digit-reversed spectrum (pos<S-1>)
+  static BPM_DEV void fwd(float2 (&a)[16], float2 (&b)[16], float2* buf, int stride, int estride,
+                          const float2* tw, int t, int g) {
+    sfwd<0>(a, b, tw, t);
+    if constexpr (S > 1) {
+      xchg<0, 1>(a, b, buf, stride, estride, t, g);
+      sfwd<1>(a, b, tw, t);
+    }
+    if constexpr (S > 2) {
+      xchg<1, 2>(a, b, buf, stride, estride, t, g);
+      sfwd<2>(a, b, tw, t);
+    }
+    static_assert(S <= 3, "3D transforms up to 4096 points");
+  }
+
+  static BPM_DEV void inv(float2 (&a)[16], float2 (&b)[16], float2* buf, int stride, int estride,
+                          const float2* tw, int t, int g) {
+    if constexpr (S > 2) {
+      sinv<2>(a, b, tw, t);
+      xchg<2, 1>(a, b, buf, stride, estride, t, g);
+    }
+    if constexpr (S > 1) {
+      sinv<1>(a, b, tw, t);
+      xchg<1, 0>(a, b, buf, stride, estride, t, g);
+    }
+    sinv<0>(a, b, tw, t);
+  }
+};
+
+constexpr int kRowThreads = 256;
+
+// Row pass.  MODE 0: natural x in, forward x out (sigma order).  MODE 1: sigma
+// in, inverse x, coupling, forward x, sigma out.  MODE 2: sigma in, inverse x,
+// coupling, natural x out.
+template <int NX, int MODE>
+__global__ void __launch_bounds__(kRowThreads, 2) row_pass_kernel(Pass3DArgs A) {
+  constexpr int T = NX / 16;
+  constexpr int R = kRowThreads / T;  // rows per block
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* smem = reinterpret_cast<float2*>(smem_raw);
+  const int g = threadIdx.x / T;
+  const int t = threadIdx.x % T;
+  const int ch = blockIdx.y;
+  const int y = blockIdx.x * R + g;
+  if (y >= A.ny) return;  // whole groups only (ny is a multiple of R for supported sizes)
+  float2* buf = smem + size_t(g) * 2 * NX;
+  const size_t row = (size_t(ch) * A.ny + y) * NX;
+  float2* e0 = A.e0 + row;
+  float2* eh = A.eh + row;
+  float2 a[16], b[16];
+  if constexpr (MODE == 0) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      a[k] = e0[t + T * k];
+      b[k] = eh[t + T * k];
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      a[k] = e0[k * T + t];
+      b[k] = eh[k * T + t];
+    }
+    Fft2Env<NX>::inv(a, b, buf, 1, NX, A.twx, t, g);
+    const float2* crow = A.cfield + (size_t(A.z) * A.ny + y) * NX;
+    const ChannelCoef cf = A.coef[ch];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const float2 c = __ldg(crow + t + T * k);
+      const bool in = (c.x != 0.f) || (c.y != 0.f);
+      const float ahx = in ? cf.a_hi.x : 1.f, ahy = in ? cf.a_hi.y : 0.f;
+      const float alx = in ? cf.a_lo.x : 0.f, aly = in ? cf.a_lo.y : 0.f;
+      const float2 bpc = c_mul(cf.bp, c);
+      const float2 bmc = c_mulc(cf.bm, c);
+      const float2 p = a[k], m = b[k];
+      a[k] = make_float2(
+          fmaf(ahx, p.x, fmaf(-ahy, p.y, fmaf(bpc.x, m.x, fmaf(-bpc.y, m.y, fmaf(alx, p.x, -aly * p.y))))),
+          fmaf(ahx, p.y, fmaf(ahy, p.x, fmaf(bpc.x, m.y, fmaf(bpc.y, m.x, fmaf(alx, p.y, aly * p.x))))));
+      b[k] = make_float2(
+          fmaf(ahx, m.x, fmaf(-ahy, m.y, fmaf(bmc.x, p.x, fmaf(-bmc.y, p.y, fmaf(alx, m.x, -aly * m.y))))),
+          fmaf(ahx, m.y, fmaf(ahy, m.x, fmaf(bmc.x, p.y, fmaf(bmc.y, p.x, fmaf(alx, m.y, aly * m.x))))));
+    }
+  }
+  if constexpr (MODE == 2) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      e0[t + T * k] = a[k];
+      eh[t + T * k] = b[k];
+    }
+  } else {
+    Fft2Env<NX>::fwd(a, b, buf, 1, NX, A.twx, t, g);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      e0[k * T + t] = a[k];
+      eh[k * T + t] = b[k];
+    }
+  }
+}
+
+constexpr int kColThreads = 256;
+
+// Column pass over a tile of W = 256 / (NY/16) stored x-frequency columns.
+template <int NY>
+__global__ void __launch_bounds__(kColThreads, 2) col_pass_kernel(Pass3DArgs A) {
+  constexpr int T = NY / 16;
+  constexpr int W = kColThreads / T;  // columns per block
+  constexpr int LD = W + 1;           // padded row length of the tile
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* tile = reinterpret_cast<float2*>(smem_raw);  // [env][NY][LD]
+  constexpr int ES = NY * LD;
+  const int ch = blockIdx.y;
+  const int c0 = blockIdx.x * W;
+  const size_t base = size_t(ch) * NY * A.nx;
+  // coalesced load of W columns x NY rows of both envelopes
+  for (int i = threadIdx.x; i < 2 * NY * W; i += kColThreads) {
+    const int e = i / (NY * W);
+    const int r = (i / W) % NY;
+    const int w = i % W;
+    const float2* src = (e == 0 ? A.e0 : A.eh) + base + size_t(r) * A.nx + c0 + w;
+    tile[e * ES + r * LD + w] = *src;
+  }
+  __syncthreads();
+  const int g = threadIdx.x / T;  // column in the tile
+  const int t = threadIdx.x % T;
+  float2* col = tile + g;
+  float2 a[16], b[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    a[k] = col[(t + T * k) * LD];
+    b[k] = col[ES + (t + T * k) * LD];
+  }
+  // buf addressing: element p at col[swz(p) * LD], envelope offset ES
+  Fft2Env<NY>::fwd(a, b, col, LD, ES, A.twy, t, g);
+  const int cs = c0 + g;  // stored column index
+  const float4 an0 = __ldg(A.anchor + (size_t(ch) * 2 + 0) * A.nx + cs);
+  const float4 an1 = __ldg(A.anchor + (size_t(ch) * 2 + 1) * A.nx + cs);
+  const float g0 = __ldg(A.gcorr + (size_t(ch) * 2 + 0) * A.nx + cs);
+  const float g1 = __ldg(A.gcorr + (size_t(ch) * 2 + 1) * A.nx + cs);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const float2 qd = __ldg(A.qy + 16 * t + k);  // {qy^2, -delta_y} at spectrum position 16 t + k
+    const float c0r = qd.x * g0, c1r = qd.x * g1;
+    float2 v = c_mul2(a[k], an0);
+    const float2 e0 = make_float2(fmaf(-0.5f * c0r, c0r, qd.y), c0r);
+    a[k] = make_float2(fmaf(v.x, e0.x, fmaf(-v.y, e0.y, v.x)), fmaf(v.x, e0.y, fmaf(v.y, e0.x, v.y)));
+    v = c_mul2(b[k], an1);
+    const float2 e1 = make_float2(fmaf(-0.5f * c1r, c1r, qd.y), c1r);
+    b[k] = make_float2(fmaf(v.x, e1.x, fmaf(-v.y, e1.y, v.x)), fmaf(v.x, e1.y, fmaf(v.y, e1.x, v.y)));
+  }
+  Fft2Env<NY>::inv(a, b, col, LD, ES, A.twy, t, g);
+  g3_sync<T>(g);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    col[(t + T * k) * LD] = a[k];
+    col[ES + (t + T * k) * LD] = b[k];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * NY * W; i += kColThreads) {
+    const int e = i / (NY * W);
+    const int r = (i / W) % NY;
+    const int w = i % W;
+    float2* dst = (e == 0 ? A.e0 : A.eh) + base + size_t(r) * A.nx + c0 + w;
+    *dst = tile[e * ES + r * LD + w];
+  }
+}
+
+// Per-channel sums of |E0|^2 and |Eh|^2 over the plane (FP64), divided by the
+// incident norm.
+__global__ void reduce3d_kernel(const float2* e0, const float2* eh, long long plane,
+                                const double* inc, double* refl, double* trans) {
+  const int ch = blockIdx.x;
+  double sa = 0.0, sb = 0.0;
+  for (long long i = threadIdx.x; i < plane; i += blockDim.x) {
+    const float2 a = e0[ch * plane + i], b = eh[ch * plane + i];
+    sa += double(a.x) * a.x + double(a.y) * a.y;
+    sb += double(b.x) * b.x + double(b.y) * b.y;
+  }
+  __shared__ double ra[32], rb[32];
+  for (int off = 16; off > 0; off >>= 1) {
+    sa += __shfl_xor_sync(0xFFFFFFFFu, sa, off);
+    sb += __shfl_xor_sync(0xFFFFFFFFu, sb, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    ra[threadIdx.x / 32] = sa;
+    rb[threadIdx.x / 32] = sb;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    sa = 0.0;
+    sb = 0.0;
+    for (int w = 0; w < int(blockDim.x / 32); ++w) {
+      sa += ra[w];
+      sb += rb[w];
+    }
+    refl[ch] = sb / inc[ch];
+    trans[ch] = sa / inc[ch];
+  }
+}
+
+template <int NX, int MODE>
+size_t row_smem() {
+  return size_t(kRowThreads / (NX / 16)) * 2 * NX * sizeof(float2);
+}
+
+template <int NY>
+size_t col_smem() {
+  return size_t(2) * NY * (kColThreads / (NY / 16) + 1) * sizeof(float2);
+}
+
+template <int NX, int MODE>
+cudaError_t row_launch(const Pass3DArgs& a, int n_ch, cudaStream_t s) {
+  constexpr int R = kRowThreads / (NX / 16);
+  dim3 grid(unsigned((a.ny + R - 1) / R), unsigned(n_ch));
+  row_pass_kernel<NX, MODE><<<grid, kRowThreads, row_smem<NX, MODE>(), s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int NY>
+cudaError_t col_launch(const Pass3DArgs& a, int n_ch, cudaStream_t s) {
+  constexpr int W = kColThreads / (NY / 16);
+  dim3 grid(unsigned(a.nx / W), unsigned(n_ch));
+  col_pass_kernel<NY><<<grid, kColThreads, col_smem<NY>(), s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int NX>
+cudaError_t row_attrs() {
+  cudaError_t e = cudaSuccess, r;
+  if ((r = cudaFuncSetAttribute(row_pass_kernel<NX, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(row_smem<NX, 0>()))) != cudaSuccess) e = r;
+  if ((r = cudaFuncSetAttribute(row_pass_kernel<NX, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(row_smem<NX, 1>()))) != cudaSuccess) e = r;
+  if ((r = cudaFuncSetAttribute(row_pass_kernel<NX, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(row_smem<NX, 2>()))) != cudaSuccess) e = r;
+  return e;
+}
+
+template <int NY>
+cudaError_t col_attrs() {
+  return cudaFuncSetAttribute(col_pass_kernel<NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(col_smem<NY>()));
+}
+
+}  // namespace
+
+bool pass3d_supported(int nx, int ny) {
+  auto ok = [](int n) { return n == 256 || n == 512 || n == 1024; };
+  return ok(nx) && ok(ny);
+}
+
+cudaError_t pass3d_set_attributes() {
+  cudaError_t e = cudaSuccess, r;
+  if ((r = row_attrs<256>()) != cudaSuccess) e = r;
+  if ((r = row_attrs<512>()) != cudaSuccess) e = r;
+  if ((r = row_attrs<1024>()) != cudaSuccess) e = r;
+  if ((r = col_attrs<256>()) != cudaSuccess) e = r;
+  if ((r = col_attrs<512>()) != cudaSuccess) e = r;
+  if ((r = col_attrs<1024>()) != cudaSuccess) e = r;
+  return e;
+}
+
+cudaError_t launch_row_pass(int mode, const Pass3DArgs& a, int n_ch, cudaStream_t s) {
+#define BPM_ROW(NXV)                                          \
+  if (a.nx == NXV) {                                          \
+    if (mode == 0) return row_launch<NXV, 0>(a, n_ch, s);     \
+    if (mode == 1) return row_launch<NXV, 1>(a, n_ch, s);     \
+    return row_launch<NXV, 2>(a, n_ch, s);                    \
+  }
+  BPM_ROW(256) BPM_ROW(512) BPM_ROW(1024)
+#undef BPM_ROW
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_col_pass(const Pass3DArgs& a, int n_ch, cudaStream_t s) {
+  if (a.ny == 256) return col_launch<256>(a, n_ch, s);
+  if (a.ny == 512) return col_launch<512>(a, n_ch, s);
+  if (a.ny == 1024) return col_launch<1024>(a, n_ch, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_reduce3d(const float2* e0, const float2* eh, long long plane, int n_ch,
+                            const double* inc, double* refl, double* trans, cudaStream_t s) {
+  reduce3d_kernel<<<n_ch, 256, 0, s>>>(e0, eh, plane, inc, refl, trans);
+  return cudaGetLastError();
+}
+
+}  // namespace bpm

@@ -156,7 +156,7 @@ const DeviceInfo& device_info() {
     d.ok = true;
     if (d.cc == 103)
       d.ok = march_set_attributes() == cudaSuccess && batch_set_attributes() == cudaSuccess &&
-             setup_set_attributes() == cudaSuccess;
+             setup_set_attributes() == cudaSuccess && pass3d_set_attributes() == cudaSuccess;
   }
   cache[dev] = d;
   return cache[dev];
@@ -207,6 +207,9 @@ struct bpm_plan_s {
   double2* eh_time = nullptr;
   int* dflag = nullptr;
   double* u_tmp = nullptr;
+  float* gcorr = nullptr;        // 3D: curvature factor per column
+  float2* twy = nullptr;         // 3D: y twiddles
+  float2* qy = nullptr;          // 3D: {qy^2, 1/g_y - 1} per y-spectrum position
   const double* u_dev = nullptr;  // displacement used by the deformation setup (may be null)
   size_t bytes = 0;               // device bytes owned by the plan
 
@@ -248,9 +251,10 @@ cudaError_t dalloc(T** ptr, size_t count) {
 }
 
 void free_plan_buffers(bpm_plan p) {
-  void* ptrs[] = {p->cfield, p->e0,     p->eh,       p->tables, p->coef,    p->twiddle,
-                  p->rev,    p->gain,   p->omega,    p->weight, p->inc_norm, p->refl,
-                  p->trans,  p->eh_time, p->dflag,   p->u_tmp};
+  void* ptrs[] = {p->cfield, p->e0,      p->eh,    p->tables, p->coef,     p->twiddle,
+                  p->rev,    p->gain,    p->omega, p->weight, p->inc_norm, p->refl,
+                  p->trans,  p->eh_time, p->dflag, p->u_tmp,  p->gcorr,    p->twy,
+                  p->qy};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->ev0) cudaEventDestroy(p->ev0);
@@ -266,7 +270,8 @@ size_t plan_bytes(const bpm_grid& g, int n_ch) {
   size_t b = 0;
   b += size_t(g.nz) * plane * sizeof(float2);      // deformation factor
   b += 2 * nf * sizeof(float2);                    // E0, Eh
-  b += size_t(n_ch) * 2 * g.nx * sizeof(float4);   // propagator tables
+  b += size_t(n_ch) * 2 * g.nx * sizeof(float4);   // propagator tables (3D: column anchors)
+  if (g.dims == 3) b += size_t(n_ch) * 2 * g.nx * sizeof(float) + size_t(g.ny) * 2 * sizeof(float2);
   b += size_t(n_ch) * sizeof(ChannelCoef);
   b += size_t(g.nx) * (sizeof(float2) + sizeof(int) + sizeof(double));
   b += size_t(n_ch) * (5 * sizeof(double) + sizeof(double2));
@@ -279,8 +284,11 @@ cudaError_t enqueue_crystal(bpm_plan p) { return launch_deformation(p->sa, p->u_
 
 // Tables, coefficients and incident field from the stored pulse; march back to z = 0.
 cudaError_t enqueue_pulse(bpm_plan p) {
-  cudaError_t e = launch_tables(p->sa, p->omega, p->gain, p->rev, p->tables, p->coef, p->dflag,
-                                p->stream);
+  cudaError_t e = p->grid.dims == 3
+                      ? launch_tables3d(p->sa, p->omega, p->gain, p->rev, p->tables, p->gcorr,
+                                        p->coef, p->stream)
+                      : launch_tables(p->sa, p->omega, p->gain, p->rev, p->tables, p->coef,
+                                      p->dflag, p->stream);
   if (e != cudaSuccess) return e;
   e = launch_incident(p->sa, p->omega, p->weight, p->e0, p->eh, p->inc_norm, p->stream);
   p->z = 0;
@@ -308,11 +316,17 @@ BPM_API bpm_status bpm_plan_create(const bpm_grid* grid, int n_channels, void* c
     return fail(nullptr, BPM_ERR_INVALID_ARG, "nz, dx and dz must be positive");
   if (g.split_order != 1)
     return fail(nullptr, BPM_ERR_UNSUPPORTED, "only first-order splitting is implemented");
-  if (g.dims != 2)
-    return fail(nullptr, BPM_ERR_UNSUPPORTED, "only dims = 2 is implemented in this build");
-  if (g.ny != 1) return fail(nullptr, BPM_ERR_INVALID_ARG, "dims = 2 requires ny = 1");
-  if (!is_pow2(g.nx) || g.nx < 256 || g.nx > 8192)
-    return fail(nullptr, BPM_ERR_UNSUPPORTED, "nx must be a power of two in [256, 8192]");
+  if (g.dims == 2) {
+    if (g.ny != 1) return fail(nullptr, BPM_ERR_INVALID_ARG, "dims = 2 requires ny = 1");
+    if (!is_pow2(g.nx) || g.nx < 256 || g.nx > 8192)
+      return fail(nullptr, BPM_ERR_UNSUPPORTED, "nx must be a power of two in [256, 8192]");
+  } else if (g.dims == 3) {
+    if (!pass3d_supported(g.nx, g.ny))
+      return fail(nullptr, BPM_ERR_UNSUPPORTED, "3D: nx and ny must be 256, 512 or 1024");
+    if (!(g.dy > 0)) return fail(nullptr, BPM_ERR_INVALID_ARG, "3D: dy must be positive");
+  } else {
+    return fail(nullptr, BPM_ERR_INVALID_ARG, "dims must be 2 or 3");
+  }
   const DeviceInfo& di = device_info();
   if (di.cc != 103 && di.sm_count > 0)
     return fail(nullptr, BPM_ERR_UNSUPPORTED, "libbpm is built for sm_103a (GB300) only");
@@ -349,6 +363,11 @@ BPM_API bpm_status bpm_plan_create(const bpm_grid* grid, int n_channels, void* c
   check(dalloc(&p->trans, size_t(n_channels)), "alloc T");
   check(dalloc(&p->eh_time, nf), "alloc time response");
   check(dalloc(&p->dflag, size_t(4)), "alloc status");
+  if (g.dims == 3) {
+    check(dalloc(&p->gcorr, size_t(n_channels) * 2 * g.nx), "alloc curvature factors");
+    check(dalloc(&p->twy, size_t(g.ny)), "alloc y twiddles");
+    check(dalloc(&p->qy, size_t(g.ny)), "alloc qy table");
+  }
   if (st != BPM_OK) {
     free_plan_buffers(P);
     return st;
@@ -364,6 +383,23 @@ BPM_API bpm_status bpm_plan_create(const bpm_grid* grid, int n_channels, void* c
                         p->stream),
         "upload gain");
   check(cudaMemsetAsync(p->dflag, 0, sizeof(int) * 4, p->stream), "clear status");
+  std::vector<float2> qyt;
+  if (g.dims == 3) {
+    const FftConsts& fy = fft_consts(g.ny);
+    qyt.resize(g.ny);
+    for (int py = 0; py < g.ny; ++py) {
+      const int m = fy.rev[py];
+      const int mm = m < g.ny / 2 ? m : m - g.ny;
+      const double q = 2.0 * kPiHost * double(mm) / (double(g.ny) * g.dy);
+      qyt[py] = make_float2(float(q * q), float(1.0 / fy.gain[py] - 1.0));
+    }
+    check(cudaMemcpyAsync(p->twy, fy.tw.data(), sizeof(float2) * g.ny, cudaMemcpyHostToDevice,
+                          p->stream),
+          "upload y twiddles");
+    check(cudaMemcpyAsync(p->qy, qyt.data(), sizeof(float2) * g.ny, cudaMemcpyHostToDevice,
+                          p->stream),
+          "upload qy table");
+  }
   check(cudaStreamSynchronize(p->stream), "plan upload");
   if (st != BPM_OK) {
     free_plan_buffers(P);
@@ -445,6 +481,18 @@ BPM_API bpm_status bpm_set_pulse(bpm_plan p, const double* omega, const double* 
   for (int i = 0; i < p->n_ch; ++i)
     if (!(omega[i] / 299792458.0 > 0.5 * p->sa.h))
       return fail(p, BPM_ERR_INVALID_ARG, "a channel has k <= h/2 (no Bragg solution)");
+  if (p->grid.dims == 3) {
+    // the column pass expands sqrt(K^2 - qy^2) - K to second order in
+    // c = dz qy^2 / (2K): require every K^2 > 0 and c < 1e-3 (terms dropped < 2e-10)
+    const double qxm = kPiHost / p->grid.dx + 0.5 * p->sa.h;
+    const double qym = kPiHost / p->grid.dy;
+    for (int i = 0; i < p->n_ch; ++i) {
+      const double k = omega[i] / 299792458.0;
+      const double K2 = k * k - qxm * qxm;
+      if (!(K2 > 0.0) || p->grid.dz * qym * qym / (2.0 * std::sqrt(K2)) > 1e-3)
+        return fail(p, BPM_ERR_UNSUPPORTED, "3D grid too fine for the paraxial y correction");
+    }
+  }
   p->sa.theta_i = theta_i;
   p->sa.x0 = x0;
   p->sa.w0 = w0;
@@ -496,11 +544,42 @@ BPM_API bpm_status bpm_run(bpm_plan p, int n_steps) {
   a.n_ch = p->n_ch;
   a.z0 = p->z;
   a.n_steps = n_steps;
-  int launches = 0;
+  int launches = 0, march_launches = 0;
   if (p->timing) BPM_CUDA(p, cudaEventRecord(p->ev0, p->stream), "timing event");
-  BPM_CUDA(p, launch_march(p->grid.nx, p->group, p->blocks, a, p->stream), "march kernel");
-  ++launches;
+  if (p->grid.dims == 2) {
+    BPM_CUDA(p, launch_march(p->grid.nx, p->group, p->blocks, a, p->stream), "march kernel");
+    march_launches = 1;
+  } else if (n_steps > 0) {
+    Pass3DArgs pa;
+    pa.e0 = p->e0;
+    pa.eh = p->eh;
+    pa.cfield = p->cfield;
+    pa.coef = p->coef;
+    pa.twx = p->twiddle;
+    pa.twy = p->twy;
+    pa.anchor = p->tables;
+    pa.gcorr = p->gcorr;
+    pa.qy = p->qy;
+    pa.nx = p->grid.nx;
+    pa.ny = p->grid.ny;
+    pa.z = p->z;
+    BPM_CUDA(p, launch_row_pass(0, pa, p->n_ch, p->stream), "row pass");
+    march_launches = 1;
+    for (int s = 0; s < n_steps; ++s) {
+      pa.z = p->z + s;
+      BPM_CUDA(p, launch_col_pass(pa, p->n_ch, p->stream), "column pass");
+      BPM_CUDA(p, launch_row_pass(s == n_steps - 1 ? 2 : 1, pa, p->n_ch, p->stream), "row pass");
+      march_launches += 2;
+    }
+  }
+  launches += march_launches;
   if (p->timing) BPM_CUDA(p, cudaEventRecord(p->ev1, p->stream), "timing event");
+  if (p->grid.dims == 3) {
+    BPM_CUDA(p, launch_reduce3d(p->e0, p->eh, p->plane, p->n_ch, p->inc_norm, p->refl, p->trans,
+                                p->stream),
+             "reflectivity");
+    ++launches;
+  }
   p->z += n_steps;
   p->time_valid = false;
   if (p->z == p->grid.nz) {
@@ -510,7 +589,21 @@ BPM_API bpm_status bpm_run(bpm_plan p, int n_steps) {
     p->time_valid = true;
   }
   p->stats.launches = launches;
-  p->stats.march_launches = 1;
+  p->stats.march_launches = march_launches;
+  return BPM_OK;
+}
+
+BPM_API bpm_status bpm_set_stream(bpm_plan p, void* cuda_stream) {
+  if (!p) return fail(nullptr, BPM_ERR_INVALID_ARG, "null plan");
+  cudaStream_t ns = static_cast<cudaStream_t>(cuda_stream);
+  if (ns == p->stream) return BPM_OK;
+  cudaEvent_t ev;
+  BPM_CUDA(p, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+  cudaError_t e = cudaEventRecord(ev, p->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ns, ev, 0);
+  cudaEventDestroy(ev);
+  BPM_CUDA(p, e, "stream switch");
+  p->stream = ns;
   return BPM_OK;
 }
 
@@ -606,6 +699,7 @@ namespace {
 
 struct BatchEntry {
   bpm_plan plan = nullptr;
+  cudaStream_t orig_stream = nullptr;  // restored when the ticket completes or is cancelled
   uint64_t ticket = 0;
   bool finishing = false;  // finalize enqueued, done event recorded
   bool cancelled = false;
@@ -754,34 +848,17 @@ bpm_status enqueue_round(bpm_batch b, RoundSlot& r, int chunk) {
   BPM_BCUDA(b, cudaMemcpyAsync(r.d_items, r.h_items, sizeof(BatchItem) * tmp.size(),
                                cudaMemcpyHostToDevice, b->stream), "upload items");
   BPM_BCUDA(b, cudaMemsetAsync(r.d_counter, 0, 2 * sizeof(int), b->stream), "clear queue");
-  // split the SMs between the two queues in proportion to their work so that
-  // both drain together (one block per SM for either kernel)
-  double w_small = 0.0, w_big = 0.0;
-  for (auto& t : tmp) (t.big ? w_big : w_small) += t.cost;
-  int big_blocks = 0, small_blocks = 0;
-  if (n_big > 0 && n_small > 0) {
-    big_blocks = int(std::lround(di.sm_count * w_big / (w_big + w_small)));
-    big_blocks = std::max(1, std::min(big_blocks, di.sm_count - 1));
-    small_blocks = di.sm_count - big_blocks;
-  } else {
-    big_blocks = di.sm_count;
-    small_blocks = di.sm_count;
-  }
-  big_blocks = std::min(big_blocks, n_big);
-  small_blocks = std::min(small_blocks, n_small);
-  if (n_big > 0) {
-    BPM_BCUDA(b, cudaEventRecord(b->fork, b->stream), "fork");
-    BPM_BCUDA(b, cudaStreamWaitEvent(b->side, b->fork, 0), "fork wait");
+  // The Nx = 8192 queue (the longest items) runs first on every SM, then the
+  // queue of smaller items on every SM: longest-processing-time-first across
+  // both queues, with an idle tail of at most one item per queue.
+  if (n_big > 0)
     BPM_BCUDA(b, launch_batch(r.d_plans, r.d_items + n_small, n_big, r.d_counter + 1, true,
-                              big_blocks, b->side),
+                              std::min(n_big, di.sm_count), b->stream),
               "batch kernel (Nx 8192)");
-    BPM_BCUDA(b, cudaEventRecord(b->join, b->side), "join");
-  }
   if (n_small > 0)
-    BPM_BCUDA(b, launch_batch(r.d_plans, r.d_items, n_small, r.d_counter, false, small_blocks,
-                              b->stream),
+    BPM_BCUDA(b, launch_batch(r.d_plans, r.d_items, n_small, r.d_counter, false,
+                              std::min(n_small, di.sm_count), b->stream),
               "batch kernel");
-  if (n_big > 0) BPM_BCUDA(b, cudaStreamWaitEvent(b->stream, b->join, 0), "join wait");
   BPM_BCUDA(b, cudaEventRecord(r.free_ev, b->stream), "round event");
   r.used = true;
   b->last_items[0] = n_small;
@@ -840,6 +917,8 @@ BPM_API bpm_status bpm_batch_submit(bpm_batch b, bpm_plan p, uint64_t* ticket) {
     if (e.plan == p) return bfail(b, BPM_ERR_STATE, "plan already in the batch");
   if (b->budget && b->used + p->bytes > b->budget)
     return bfail(b, BPM_ERR_OOM, "not admitted: HBM budget exhausted");
+  BatchEntry e;
+  e.orig_stream = p->stream;
   if (p->stream != b->stream) {
     // order the plan's setup work before the batch's rounds, then adopt the batch stream
     cudaEvent_t ev;
@@ -849,7 +928,6 @@ BPM_API bpm_status bpm_batch_submit(bpm_batch b, bpm_plan p, uint64_t* ticket) {
     cudaEventDestroy(ev);
     p->stream = b->stream;
   }
-  BatchEntry e;
   e.plan = p;
   e.ticket = b->next_ticket++;
   b->entries.push_back(e);
@@ -885,6 +963,9 @@ BPM_API bpm_status bpm_batch_poll(bpm_batch b, uint64_t ticket, int* done) {
     if (q == cudaErrorNotReady) return BPM_OK;
     if (q != cudaSuccess) return bfail(b, BPM_ERR_CUDA, cudaGetErrorString(q));
     cudaEventDestroy(e.done);
+    e.done = nullptr;
+    // no round enqueued after the completing one touches this plan
+    e.plan->stream = e.orig_stream;
     b->used -= e.plan->bytes;
     b->finished[ticket] = 1;
     b->entries.erase(b->entries.begin() + long(i));
@@ -902,6 +983,9 @@ BPM_API bpm_status bpm_batch_cancel(bpm_batch b, uint64_t ticket) {
     if (e.finishing) return bfail(b, BPM_ERR_STATE, "ticket already finishing");
     // rounds already enqueued may still touch the plan: wait for them
     BPM_BCUDA(b, cudaStreamSynchronize(b->stream), "cancel");
+    if (b->side) BPM_BCUDA(b, cudaStreamSynchronize(b->side), "cancel");
+    e.plan->stream = e.orig_stream;
+    if (e.done) cudaEventDestroy(e.done);
     b->used -= e.plan->bytes;
     b->finished[ticket] = 2;
     b->entries.erase(b->entries.begin() + long(i));

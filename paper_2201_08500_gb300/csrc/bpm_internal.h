@@ -35,6 +35,20 @@ struct MarchArgs {
   int n_steps;
 };
 
+// Arguments of the 3D row / column passes (bpm_3d.cu).
+struct Pass3DArgs {
+  float2* e0;                // [n_ch][ny][nx]
+  float2* eh;
+  const float2* cfield;      // [nz][ny][nx]
+  const ChannelCoef* coef;   // [n_ch]
+  const float2* twx;         // [nx] exp(-2 pi i k / nx)
+  const float2* twy;         // [ny]
+  const float4* anchor;      // [n_ch][2][nx] FP32 hi + lo of exp(i dz (K - k)) / (nx ny g_x)
+  const float* gcorr;        // [n_ch][2][nx] -dz / (2 K)
+  const float2* qy;          // [ny] {qy^2, 1/g_y - 1} at y-spectrum positions
+  int nx, ny, z;
+};
+
 // Per-plan device pointers used by the setup kernels.
 struct SetupArgs {
   int nx, ny, nz, n_ch, dims;
@@ -77,7 +91,19 @@ int march_max_group(int n);
 size_t march_smem_bytes(int n, int group);
 cudaError_t launch_march(int n, int group, int blocks, const MarchArgs& a, cudaStream_t s);
 
+// 3D passes (bpm_3d.cu).  mode: 0 forward x only, 1 inverse x + coupling +
+// forward x, 2 inverse x + coupling.
+bool pass3d_supported(int nx, int ny);
+cudaError_t pass3d_set_attributes();
+cudaError_t launch_row_pass(int mode, const Pass3DArgs& a, int n_ch, cudaStream_t s);
+cudaError_t launch_col_pass(const Pass3DArgs& a, int n_ch, cudaStream_t s);
+cudaError_t launch_reduce3d(const float2* e0, const float2* eh, long long plane, int n_ch,
+                            const double* inc, double* refl, double* trans, cudaStream_t s);
+
 // Setup launchers (bpm_setup.cu).
+cudaError_t launch_tables3d(const SetupArgs& sa, const double* omega, const double* gainx,
+                            const int* revx, float4* anchor, float* gcorr, ChannelCoef* coef,
+                            cudaStream_t s);
 cudaError_t launch_deformation(const SetupArgs& sa, const double* u_dev, float2* cfield,
                                cudaStream_t s);
 cudaError_t launch_tables(const SetupArgs& sa, const double* omega, const double* gain,

@@ -110,6 +110,31 @@ __device__ void bessel_j0_g1(dc w2, dc* j0, dc* g1) {
   *g1 = s1;
 }
 
+// Coupling coefficients of Eq. fov10 for one channel: w^2 = (k dz / cos a)^2
+// chi_h chi_hbar, a = J0 e^{i phi} e^{w^2/8} (Zassenhaus), b+ = i G1 e^{i phi}
+// k dz chi_hbar / (2 cos a), b- likewise with chi_h; a split into hi + lo.
+__device__ ChannelCoef channel_coef(const SetupArgs& sa, double kdz, double cos_a) {
+  const dc chi0 = dmk(sa.chi0_re, sa.chi0_im);
+  const dc chih = dmk(sa.chih_re, sa.chih_im);
+  const dc chihb = dmk(sa.chihb_re, sa.chihb_im);
+  const double r = kdz / cos_a;
+  const dc w2 = dscale(dmul(chih, chihb), r * r);
+  const dc phase0 = dexp(dmul(dmk(0, 1), dscale(chi0, kdz / (2.0 * cos_a))));
+  dc j0, g1;
+  bessel_j0_g1(w2, &j0, &g1);
+  const dc zf = sa.zassenhaus ? dexp(dscale(w2, 0.125)) : dmk(1, 0);
+  const dc a = dmul(dmul(j0, phase0), zf);
+  const dc ig1p = dmul(dmk(0, 1), dmul(g1, phase0));
+  const dc bp = dmul(ig1p, dscale(chihb, kdz / (2.0 * cos_a)));
+  const dc bm = dmul(ig1p, dscale(chih, kdz / (2.0 * cos_a)));
+  ChannelCoef c;
+  c.a_hi = to_f2(a);
+  c.a_lo = make_float2(float(a.re - double(c.a_hi.x)), float(a.im - double(c.a_hi.y)));
+  c.bp = to_f2(bp);
+  c.bm = to_f2(bm);
+  return c;
+}
+
 // One block per channel.  Tables are written in the march kernel's order:
 // [ch][env][k][t] for the spectrum position p = 16 t + k, env 0 = E0 (+h/2), 1 = Eh (-h/2).
 __global__ void tables_kernel(SetupArgs sa, const double* __restrict__ omega,
@@ -127,27 +152,7 @@ __global__ void tables_kernel(SetupArgs sa, const double* __restrict__ omega,
   }
   const double cos_a = sqrt(1.0 - s_ratio * s_ratio);  // cos(alpha), Eq. fov3
   const double kdz = k * sa.dz;
-  if (threadIdx.x == 0) {
-    const dc chi0 = dmk(sa.chi0_re, sa.chi0_im);
-    const dc chih = dmk(sa.chih_re, sa.chih_im);
-    const dc chihb = dmk(sa.chihb_re, sa.chihb_im);
-    const double r = kdz / cos_a;
-    const dc w2 = dscale(dmul(chih, chihb), r * r);
-    const dc phase0 = dexp(dmul(dmk(0, 1), dscale(chi0, kdz / (2.0 * cos_a))));
-    dc j0, g1;
-    bessel_j0_g1(w2, &j0, &g1);
-    const dc zf = sa.zassenhaus ? dexp(dscale(w2, 0.125)) : dmk(1, 0);
-    const dc a = dmul(dmul(j0, phase0), zf);
-    const dc ig1p = dmul(dmk(0, 1), dmul(g1, phase0));
-    const dc bp = dmul(ig1p, dscale(chihb, kdz / (2.0 * cos_a)));
-    const dc bm = dmul(ig1p, dscale(chih, kdz / (2.0 * cos_a)));
-    ChannelCoef c;
-    c.a_hi = to_f2(a);
-    c.a_lo = make_float2(float(a.re - double(c.a_hi.x)), float(a.im - double(c.a_hi.y)));
-    c.bp = to_f2(bp);
-    c.bm = to_f2(bm);
-    coef[ch] = c;
-  }
+  if (threadIdx.x == 0) coef[ch] = channel_coef(sa, kdz, cos_a);
   float4* out = tables + size_t(ch) * 2 * n;
   for (int p = threadIdx.x; p < n; p += blockDim.x) {
     const double q = qbin(rev[p], n, sa.dx);
@@ -160,6 +165,38 @@ __global__ void tables_kernel(SetupArgs sa, const double* __restrict__ omega,
       const float2 hi = to_f2(P);
       const float2 lo = make_float2(float(P.re - double(hi.x)), float(P.im - double(hi.y)));
       out[size_t(env) * n + size_t(kk) * T + t] = make_float4(hi.x, hi.y, lo.x, lo.y);
+    }
+  }
+}
+
+// 3D: per channel and stored x-frequency column cs (px = 16 (cs % T) + cs / T),
+// the anchor exp(i dz (K - k)) / (nx ny g_x(px)), K = sqrt(k^2 - (qx +- h/2)^2),
+// as FP32 hi + lo, and the curvature factor -dz / (2 K) of the qy correction.
+__global__ void tables3d_kernel(SetupArgs sa, const double* __restrict__ omega,
+                                const double* __restrict__ gainx, const int* __restrict__ revx,
+                                float4* anchor, float* gcorr, ChannelCoef* coef) {
+  const int ch = blockIdx.x;
+  const int n = sa.nx;
+  const int T = n / 16;
+  const double k = omega[ch] / kC;
+  const double half_h = 0.5 * sa.h;
+  const double s_ratio = half_h / k;
+  const double cos_a = sqrt(1.0 - s_ratio * s_ratio);
+  if (threadIdx.x == 0) coef[ch] = channel_coef(sa, k * sa.dz, cos_a);
+  for (int cs = threadIdx.x; cs < n; cs += blockDim.x) {
+    const int px = 16 * (cs % T) + cs / T;
+    const double qx = qbin(revx[px], n, sa.dx);
+    const double scale = 1.0 / (double(n) * double(sa.ny) * gainx[px]);
+    for (int env = 0; env < 2; ++env) {
+      const double Q = env == 0 ? qx + half_h : qx - half_h;
+      const double K2 = k * k - Q * Q;
+      dc P = tilted_propagator(k, Q * Q, sa.dz);
+      P = dscale(P, scale);
+      const float2 hi = to_f2(P);
+      const float2 lo = make_float2(float(P.re - double(hi.x)), float(P.im - double(hi.y)));
+      const size_t o = (size_t(ch) * 2 + env) * n + cs;
+      anchor[o] = make_float4(hi.x, hi.y, lo.x, lo.y);
+      gcorr[o] = K2 > 0.0 ? float(-sa.dz / (2.0 * sqrt(K2))) : 0.f;
     }
   }
 }
@@ -290,6 +327,13 @@ cudaError_t launch_tables(const SetupArgs& sa, const double* omega, const double
                           const int* rev, float4* tables, ChannelCoef* coef, int* bad,
                           cudaStream_t s) {
   tables_kernel<<<sa.n_ch, 256, 0, s>>>(sa, omega, gain, rev, tables, coef, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tables3d(const SetupArgs& sa, const double* omega, const double* gainx,
+                            const int* revx, float4* anchor, float* gcorr, ChannelCoef* coef,
+                            cudaStream_t s) {
+  tables3d_kernel<<<sa.n_ch, 256, 0, s>>>(sa, omega, gainx, revx, anchor, gcorr, coef);
   return cudaGetLastError();
 }
 

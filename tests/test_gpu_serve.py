@@ -1,0 +1,65 @@
+"""GPU tests of the continuous-batching server (serve.py).
+
+Requests arrive (Poisson) while others are on the GPU, are admitted as slots and
+device memory free up, and share persistent launches; each result must be the
+same as the request run alone (the same per-channel code runs either way, so
+the comparison is bitwise)."""
+import numpy as np
+import pytest
+
+from paper_2201_08500_gb300 import bpm, serve, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def requests(n_probe=30, seed=7, rate=150.0):
+    import torch
+    rng = np.random.default_rng(seed)
+    works = [workloads.probe(rng, idx=i) for i in range(n_probe)]
+    for i, (nx, nz, nch, kind) in enumerate([(1024, 160, 24, "bent"), (2048, 120, 9, "random"),
+                                             (4096, 80, 3, "perfect"), (8192, 60, 2, "random")]):
+        w = workloads.mixed_instance(rng, nx=nx, nz=nz, n_ch=nch, kind=kind, idx=100 + i)
+        w.x0 = w.x_surface - 30 * w.dx
+        w.w0 = 10 * w.dx
+        works.insert(int(rng.integers(0, len(works))), w)
+    t = serve.poisson_arrivals(len(works), rate, seed)
+    return [serve.Request(i, w, None if w.u is None else torch.from_numpy(w.u).cuda(), float(a))
+            for i, (w, a) in enumerate(zip(works, t))]
+
+
+def alone(req):
+    w = req.work
+    p = bpm.plan_from_workload(w, u=req.u_dev)
+    p.run()
+    out = p.reflectivity()[0], p.eh()
+    p.close()
+    return out
+
+
+@pytest.mark.parametrize("budget_gb", [64.0, 0.25])
+def test_served_results_equal_alone(budget_gb):
+    import torch
+    torch.cuda.set_device(0)
+    reqs = requests()
+    srv = serve.Server(hbm_budget_bytes=int(budget_gb * 2 ** 30), chunk=64)
+    srv.serve(reqs)
+    stats = serve.summarize(reqs)
+    srv.close()
+    assert all(r.done_at >= r.arrival for r in reqs)
+    assert stats["p99_ms"] >= stats["p50_ms"] > 0
+    for r in reqs:
+        R, eh = alone(r)
+        assert np.array_equal(r.R, R), r.work.name
+        assert np.array_equal(r.eh, eh), r.work.name
+    if budget_gb < 1:
+        assert srv.n_slots < len(reqs)  # slots were reused under the tight budget
+
+
+def test_plain_server_matches_too():
+    import torch
+    torch.cuda.set_device(0)
+    reqs = requests(n_probe=8, seed=3, rate=400.0)
+    serve.serve_plain(reqs)
+    for r in reqs:
+        R, eh = alone(r)
+        assert np.array_equal(r.R, R) and np.array_equal(r.eh, eh)

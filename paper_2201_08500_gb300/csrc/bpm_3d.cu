@@ -3,20 +3,24 @@
 // streams both envelopes through HBM in two passes (Eq. fov4 with the 2D
 // transverse Laplacian, Eq. fov10 coupling):
 //
-//   column pass : for a tile of W x-frequency columns, staged through padded
-//                 shared memory: forward y-FFT, multiply by the tilted
-//                 propagator p+-(qx, qy), inverse y-FFT, write back;
+//   column pass : per x-frequency column (contiguous in memory): forward
+//                 y-FFT, multiply by the tilted propagator p+-(qx, qy), inverse
+//                 y-FFT, write back;
 //   row pass    : per row y: inverse x-FFT, pointwise coupling with
 //                 c(x, y, z_n) = Pi(x) exp(+i h u(x, y, z_n)), then the next
 //                 step's forward x-FFT, write back.
 //
-// Between passes the fields are stored as [ch][y][sigma(px)]: the x-spectrum in
-// the FFT's digit-reversed positions px, permuted by sigma(px) = (px % 16) T +
-// px / 16 (T = Nx / 16) so that the row FFT's register layout (thread t holds
-// px = 16 t + k) loads and stores coalesced.  A run of n steps is: one row pass
-// (forward x of the x-space fields), then n x (column pass, row pass); the
-// last row pass leaves natural x order.  Traffic: 2 passes x 2 envelopes x
-// (8 B read + 8 B write) = 64 B per cell-update.
+// Between passes the fields are stored transposed, [ch][c][y]: c = sigma(px) is
+// the x-spectrum position px of the FFT's digit-reversed order permuted by
+// sigma(px) = (px % 16) T + px / 16 (T = Nx / 16), which is the order of the row
+// FFT's registers (thread t holds px = 16 t + k at c = k T + t).  Columns are
+// then contiguous for the column pass, which loads them straight into
+// registers; the row pass does the transposition: a block of R rows stages its
+// [c][R + 1] tile in shared memory (64-byte segments per column in HBM), and
+// each row's FFT exchanges through its own tile column.  A run of n steps is
+// one row pass (forward x of the natural-order fields), then n x (column pass,
+// row pass); the last row pass writes natural [ch][y][x] order.  Traffic:
+// 2 passes x 2 envelopes x (8 B read + 8 B write) = 64 B per cell-update.
 //
 // Propagator: p(qx, qy) = exp(i dz [sqrt(K^2 - qy^2) - k]), K^2 = k^2 - (qx +- h/2)^2,
 // written as an FP64 anchor exp(i dz [K - k]) per column (FP32 hi + lo, with
@@ -52,14 +56,18 @@ struct Fft2Env {
   static constexpr int T = Gm::T;
   static constexpr int S = Gm::S;
 
+  // Offset of stage s in the thread-ordered twiddle table (see twiddle_order).
+  __host__ __device__ static constexpr int tw_off(int s) {
+    return s == 0 ? 0 : tw_off(s - 1) + 15 * Gm::LN(s - 1);
+  }
+
   template <int s>
   static BPM_DEV void twid(float2 (&a)[16], float2 (&b)[16], const float2* tw, int t, bool inv) {
     constexpr int ln = Gm::LN(s);
-    constexpr int stride = N / Gm::L(s);
-    const int j = t % ln;
+    const float2* ts = tw + tw_off(s) + (t % ln);
 #pragma unroll
     for (int m = 1; m < 16; ++m) {
-      const float2 w = __ldg(tw + stride * j * m);
+      const float2 w = __ldg(ts + (m - 1) * ln);  // W_L(s)^(j m), consecutive threads adjacent
       a[m] = inv ? c_mulc(a[m], w) : c_mul(a[m], w);
       b[m] = inv ? c_mulc(b[m], w) : c_mul(b[m], w);
     }
@@ -139,38 +147,67 @@ struct Fft2Env {
 
 constexpr int kRowThreads = 256;
 
-// Row pass.  MODE 0: natural x in, forward x out (sigma order).  MODE 1: sigma
-// in, inverse x, coupling, forward x, sigma out.  MODE 2: sigma in, inverse x,
-// coupling, natural x out.
+// Row pass over R = 256 / T rows y0 .. y0 + R - 1 of one channel (T = NX/16).
+// MODE 0: natural rows (e0, eh) in, forward x, transposed (s0, sh) out.
+// MODE 1: transposed in, inverse x, coupling, forward x, transposed out (in
+// place: every block reads and writes only its own rows of each column).
+// MODE 2: transposed in, inverse x, coupling, natural rows out.
 template <int NX, int MODE>
 __global__ void __launch_bounds__(kRowThreads, 2) row_pass_kernel(Pass3DArgs A) {
   constexpr int T = NX / 16;
   constexpr int R = kRowThreads / T;  // rows per block
+  constexpr int LD = R + 1;           // padded tile row (one column c)
+  constexpr int ES = NX * LD;         // envelope offset in the tile
+  constexpr int HALF = R / 2;         // float4 (two y values) per column segment
+  constexpr int VEC = 2 * NX * HALF / kRowThreads;
+  static_assert(VEC * kRowThreads == 2 * NX * HALF, "tile split");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* smem = reinterpret_cast<float2*>(smem_raw);
+  float2* tile = reinterpret_cast<float2*>(smem_raw);  // [env][NX][LD]
   const int g = threadIdx.x / T;
   const int t = threadIdx.x % T;
   const int ch = blockIdx.y;
-  const int y = blockIdx.x * R + g;
-  if (y >= A.ny) return;  // whole groups only (ny is a multiple of R for supported sizes)
-  float2* buf = smem + size_t(g) * 2 * NX;
-  const size_t row = (size_t(ch) * A.ny + y) * NX;
-  float2* e0 = A.e0 + row;
-  float2* eh = A.eh + row;
+  const int y0 = blockIdx.x * R;
+  const int y = y0 + g;
+  const size_t chb = size_t(ch) * A.ny * NX;
+  float2* rowbuf = tile + g;  // this row's exchange column, stride LD, envelopes ES apart
   float2 a[16], b[16];
   if constexpr (MODE == 0) {
+    const float2* e0 = A.e0 + chb + size_t(y) * NX;
+    const float2* eh = A.eh + chb + size_t(y) * NX;
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
       a[k] = e0[t + T * k];
       b[k] = eh[t + T * k];
     }
   } else {
+    // transposed load: column c, rows y0 .. y0 + R - 1 (R x 8 bytes contiguous)
+    float4 v[VEC];
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      const int i = threadIdx.x + j * kRowThreads;
+      const int e = i / (NX * HALF);
+      const int c = (i / HALF) % NX;
+      const int h = i % HALF;
+      const float2* src = (e == 0 ? A.s0 : A.sh) + chb + size_t(c) * A.ny + y0 + 2 * h;
+      v[j] = __ldg(reinterpret_cast<const float4*>(src));
+    }
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      const int i = threadIdx.x + j * kRowThreads;
+      const int e = i / (NX * HALF);
+      const int c = (i / HALF) % NX;
+      const int h = i % HALF;
+      float2* d = tile + e * ES + c * LD + 2 * h;
+      d[0] = make_float2(v[j].x, v[j].y);
+      d[1] = make_float2(v[j].z, v[j].w);
+    }
+    __syncthreads();
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
-      a[k] = e0[k * T + t];
-      b[k] = eh[k * T + t];
+      a[k] = rowbuf[(k * T + t) * LD];
+      b[k] = rowbuf[ES + (k * T + t) * LD];
     }
-    Fft2Env<NX>::inv(a, b, buf, 1, NX, A.twx, t, g);
+    Fft2Env<NX>::inv(a, b, rowbuf, LD, ES, A.twx, t, g);
     const float2* crow = A.cfield + (size_t(A.z) * A.ny + y) * NX;
     const ChannelCoef cf = A.coef[ch];
 #pragma unroll
@@ -191,85 +228,88 @@ __global__ void __launch_bounds__(kRowThreads, 2) row_pass_kernel(Pass3DArgs A) 
     }
   }
   if constexpr (MODE == 2) {
+    float2* e0 = A.e0 + chb + size_t(y) * NX;
+    float2* eh = A.eh + chb + size_t(y) * NX;
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
       e0[t + T * k] = a[k];
       eh[t + T * k] = b[k];
     }
   } else {
-    Fft2Env<NX>::fwd(a, b, buf, 1, NX, A.twx, t, g);
+    Fft2Env<NX>::fwd(a, b, rowbuf, LD, ES, A.twx, t, g);
+    g3_sync<T>(g);
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
-      e0[k * T + t] = a[k];
-      eh[k * T + t] = b[k];
+      rowbuf[(k * T + t) * LD] = a[k];
+      rowbuf[ES + (k * T + t) * LD] = b[k];
+    }
+    __syncthreads();
+    float4 v[VEC];
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      const int i = threadIdx.x + j * kRowThreads;
+      const int e = i / (NX * HALF);
+      const int c = (i / HALF) % NX;
+      const int h = i % HALF;
+      const float2* d = tile + e * ES + c * LD + 2 * h;
+      v[j] = make_float4(d[0].x, d[0].y, d[1].x, d[1].y);
+    }
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      const int i = threadIdx.x + j * kRowThreads;
+      const int e = i / (NX * HALF);
+      const int c = (i / HALF) % NX;
+      const int h = i % HALF;
+      float2* dst = (e == 0 ? A.s0 : A.sh) + chb + size_t(c) * A.ny + y0 + 2 * h;
+      *reinterpret_cast<float4*>(dst) = v[j];
     }
   }
 }
 
 constexpr int kColThreads = 256;
 
-// Column pass over a tile of W = 256 / (NY/16) stored x-frequency columns.
+// Column pass: each group of T = NY/16 threads transforms both envelopes of one
+// stored column c, contiguous in the transposed layout.
 template <int NY>
 __global__ void __launch_bounds__(kColThreads, 2) col_pass_kernel(Pass3DArgs A) {
   constexpr int T = NY / 16;
   constexpr int W = kColThreads / T;  // columns per block
-  constexpr int LD = W + 1;           // padded row length of the tile
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* tile = reinterpret_cast<float2*>(smem_raw);  // [env][NY][LD]
-  constexpr int ES = NY * LD;
-  const int ch = blockIdx.y;
-  const int c0 = blockIdx.x * W;
-  const size_t base = size_t(ch) * NY * A.nx;
-  // coalesced load of W columns x NY rows of both envelopes
-  for (int i = threadIdx.x; i < 2 * NY * W; i += kColThreads) {
-    const int e = i / (NY * W);
-    const int r = (i / W) % NY;
-    const int w = i % W;
-    const float2* src = (e == 0 ? A.e0 : A.eh) + base + size_t(r) * A.nx + c0 + w;
-    tile[e * ES + r * LD + w] = *src;
-  }
-  __syncthreads();
-  const int g = threadIdx.x / T;  // column in the tile
+  const int g = threadIdx.x / T;
   const int t = threadIdx.x % T;
-  float2* col = tile + g;
+  const int ch = blockIdx.y;
+  const int cs = blockIdx.x * W + g;
+  float2* buf = reinterpret_cast<float2*>(smem_raw) + size_t(g) * 2 * NY;
+  const size_t colb = (size_t(ch) * A.nx + cs) * NY;
+  float2* e0 = A.s0 + colb;
+  float2* eh = A.sh + colb;
   float2 a[16], b[16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
-    a[k] = col[(t + T * k) * LD];
-    b[k] = col[ES + (t + T * k) * LD];
+    a[k] = e0[t + T * k];
+    b[k] = eh[t + T * k];
   }
-  // buf addressing: element p at col[swz(p) * LD], envelope offset ES
-  Fft2Env<NY>::fwd(a, b, col, LD, ES, A.twy, t, g);
-  const int cs = c0 + g;  // stored column index
+  Fft2Env<NY>::fwd(a, b, buf, 1, NY, A.twy, t, g);
   const float4 an0 = __ldg(A.anchor + (size_t(ch) * 2 + 0) * A.nx + cs);
   const float4 an1 = __ldg(A.anchor + (size_t(ch) * 2 + 1) * A.nx + cs);
   const float g0 = __ldg(A.gcorr + (size_t(ch) * 2 + 0) * A.nx + cs);
   const float g1 = __ldg(A.gcorr + (size_t(ch) * 2 + 1) * A.nx + cs);
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
-    const float2 qd = __ldg(A.qy + 16 * t + k);  // {qy^2, -delta_y} at spectrum position 16 t + k
+    const float2 qd = __ldg(A.qy + k * T + t);  // {qy^2, 1/g_y - 1} at position 16 t + k
     const float c0r = qd.x * g0, c1r = qd.x * g1;
     float2 v = c_mul2(a[k], an0);
-    const float2 e0 = make_float2(fmaf(-0.5f * c0r, c0r, qd.y), c0r);
-    a[k] = make_float2(fmaf(v.x, e0.x, fmaf(-v.y, e0.y, v.x)), fmaf(v.x, e0.y, fmaf(v.y, e0.x, v.y)));
+    const float2 f0 = make_float2(fmaf(-0.5f * c0r, c0r, qd.y), c0r);
+    a[k] = make_float2(fmaf(v.x, f0.x, fmaf(-v.y, f0.y, v.x)), fmaf(v.x, f0.y, fmaf(v.y, f0.x, v.y)));
     v = c_mul2(b[k], an1);
-    const float2 e1 = make_float2(fmaf(-0.5f * c1r, c1r, qd.y), c1r);
-    b[k] = make_float2(fmaf(v.x, e1.x, fmaf(-v.y, e1.y, v.x)), fmaf(v.x, e1.y, fmaf(v.y, e1.x, v.y)));
+    const float2 f1 = make_float2(fmaf(-0.5f * c1r, c1r, qd.y), c1r);
+    b[k] = make_float2(fmaf(v.x, f1.x, fmaf(-v.y, f1.y, v.x)), fmaf(v.x, f1.y, fmaf(v.y, f1.x, v.y)));
   }
-  Fft2Env<NY>::inv(a, b, col, LD, ES, A.twy, t, g);
-  g3_sync<T>(g);
+  Fft2Env<NY>::inv(a, b, buf, 1, NY, A.twy, t, g);
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
-    col[(t + T * k) * LD] = a[k];
-    col[ES + (t + T * k) * LD] = b[k];
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < 2 * NY * W; i += kColThreads) {
-    const int e = i / (NY * W);
-    const int r = (i / W) % NY;
-    const int w = i % W;
-    float2* dst = (e == 0 ? A.e0 : A.eh) + base + size_t(r) * A.nx + c0 + w;
-    *dst = tile[e * ES + r * LD + w];
+    e0[t + T * k] = a[k];
+    eh[t + T * k] = b[k];
   }
 }
 
@@ -308,12 +348,12 @@ __global__ void reduce3d_kernel(const float2* e0, const float2* eh, long long pl
 
 template <int NX, int MODE>
 size_t row_smem() {
-  return size_t(kRowThreads / (NX / 16)) * 2 * NX * sizeof(float2);
+  return size_t(2) * NX * (kRowThreads / (NX / 16) + 1) * sizeof(float2);
 }
 
 template <int NY>
 size_t col_smem() {
-  return size_t(2) * NY * (kColThreads / (NY / 16) + 1) * sizeof(float2);
+  return size_t(kColThreads / (NY / 16)) * 2 * NY * sizeof(float2);
 }
 
 template <int NX, int MODE>

@@ -134,6 +134,21 @@ const FftConsts& fft_consts(int n) {
   return ref;
 }
 
+// Stage twiddles W_L(s)^(j m) of an n-point transform in the order the 3D pass
+// kernels read them: for each stage s < S-1, m = 1..15, j = 0..L(s+1)-1.
+std::vector<float2> twiddle_order(int n) {
+  const FftConsts& f = fft_consts(n);
+  const int logn = ilog2i(n);
+  const int S = (logn + 3) / 4;
+  std::vector<float2> out;
+  for (int s = 0; s < S - 1; ++s) {
+    const int ls = n >> (4 * s), ln = n >> (4 * (s + 1)), stride = n / ls;
+    for (int m = 1; m < 16; ++m)
+      for (int j = 0; j < ln; ++j) out.push_back(f.tw[(size_t(stride) * j * m) % n]);
+  }
+  return out;
+}
+
 struct DeviceInfo {
   int sm_count = 0;
   int cc = 0;
@@ -208,7 +223,9 @@ struct bpm_plan_s {
   int* dflag = nullptr;
   double* u_tmp = nullptr;
   float* gcorr = nullptr;        // 3D: curvature factor per column
-  float2* twy = nullptr;         // 3D: y twiddles
+  float2* spec = nullptr;        // 3D: transposed x-spectra of both envelopes [2][ch][nx][ny]
+  float2* twy = nullptr;         // 3D: y twiddles (thread order)
+  float2* twx3 = nullptr;        // 3D: x twiddles (thread order)
   float2* qy = nullptr;          // 3D: {qy^2, 1/g_y - 1} per y-spectrum position
   const double* u_dev = nullptr;  // displacement used by the deformation setup (may be null)
   size_t bytes = 0;               // device bytes owned by the plan
@@ -254,7 +271,7 @@ void free_plan_buffers(bpm_plan p) {
   void* ptrs[] = {p->cfield, p->e0,      p->eh,    p->tables, p->coef,     p->twiddle,
                   p->rev,    p->gain,    p->omega, p->weight, p->inc_norm, p->refl,
                   p->trans,  p->eh_time, p->dflag, p->u_tmp,  p->gcorr,    p->twy,
-                  p->qy};
+                  p->qy,     p->spec,    p->twx3};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->ev0) cudaEventDestroy(p->ev0);
@@ -271,7 +288,9 @@ size_t plan_bytes(const bpm_grid& g, int n_ch) {
   b += size_t(g.nz) * plane * sizeof(float2);      // deformation factor
   b += 2 * nf * sizeof(float2);                    // E0, Eh
   b += size_t(n_ch) * 2 * g.nx * sizeof(float4);   // propagator tables (3D: column anchors)
-  if (g.dims == 3) b += size_t(n_ch) * 2 * g.nx * sizeof(float) + size_t(g.ny) * 2 * sizeof(float2);
+  if (g.dims == 3)
+    b += size_t(n_ch) * 2 * g.nx * sizeof(float) + size_t(g.ny) * 2 * sizeof(float2) +
+         2 * nf * sizeof(float2);
   b += size_t(n_ch) * sizeof(ChannelCoef);
   b += size_t(g.nx) * (sizeof(float2) + sizeof(int) + sizeof(double));
   b += size_t(n_ch) * (5 * sizeof(double) + sizeof(double2));
@@ -365,7 +384,9 @@ BPM_API bpm_status bpm_plan_create(const bpm_grid* grid, int n_channels, void* c
   check(dalloc(&p->dflag, size_t(4)), "alloc status");
   if (g.dims == 3) {
     check(dalloc(&p->gcorr, size_t(n_channels) * 2 * g.nx), "alloc curvature factors");
+    check(dalloc(&p->spec, 2 * nf), "alloc spectrum buffers");
     check(dalloc(&p->twy, size_t(g.ny)), "alloc y twiddles");
+    check(dalloc(&p->twx3, size_t(g.nx)), "alloc x twiddles");
     check(dalloc(&p->qy, size_t(g.ny)), "alloc qy table");
   }
   if (st != BPM_OK) {
@@ -391,11 +412,17 @@ BPM_API bpm_status bpm_plan_create(const bpm_grid* grid, int n_channels, void* c
       const int m = fy.rev[py];
       const int mm = m < g.ny / 2 ? m : m - g.ny;
       const double q = 2.0 * kPiHost * double(mm) / (double(g.ny) * g.dy);
-      qyt[py] = make_float2(float(q * q), float(1.0 / fy.gain[py] - 1.0));
+      // stored at k T + t for position py = 16 t + k (coalesced in the column pass)
+      const int Ty = g.ny / 16;
+      qyt[(py % 16) * Ty + py / 16] = make_float2(float(q * q), float(1.0 / fy.gain[py] - 1.0));
     }
-    check(cudaMemcpyAsync(p->twy, fy.tw.data(), sizeof(float2) * g.ny, cudaMemcpyHostToDevice,
+    const std::vector<float2> twy = twiddle_order(g.ny), twx = twiddle_order(g.nx);
+    check(cudaMemcpyAsync(p->twy, twy.data(), sizeof(float2) * twy.size(), cudaMemcpyHostToDevice,
                           p->stream),
           "upload y twiddles");
+    check(cudaMemcpyAsync(p->twx3, twx.data(), sizeof(float2) * twx.size(),
+                          cudaMemcpyHostToDevice, p->stream),
+          "upload x twiddles");
     check(cudaMemcpyAsync(p->qy, qyt.data(), sizeof(float2) * g.ny, cudaMemcpyHostToDevice,
                           p->stream),
           "upload qy table");
@@ -553,9 +580,11 @@ BPM_API bpm_status bpm_run(bpm_plan p, int n_steps) {
     Pass3DArgs pa;
     pa.e0 = p->e0;
     pa.eh = p->eh;
+    pa.s0 = p->spec;
+    pa.sh = p->spec + size_t(p->n_ch) * p->plane;
     pa.cfield = p->cfield;
     pa.coef = p->coef;
-    pa.twx = p->twiddle;
+    pa.twx = p->twx3;
     pa.twy = p->twy;
     pa.anchor = p->tables;
     pa.gcorr = p->gcorr;

@@ -37,15 +37,17 @@ struct MarchArgs {
 
 // Arguments of the 3D row / column passes (bpm_3d.cu).
 struct Pass3DArgs {
-  float2* e0;                // [n_ch][ny][nx]
+  float2* e0;                // [n_ch][ny][nx] natural order (x space)
   float2* eh;
+  float2* s0;                // [n_ch][nx][ny] transposed x-spectrum (working buffers)
+  float2* sh;
   const float2* cfield;      // [nz][ny][nx]
   const ChannelCoef* coef;   // [n_ch]
-  const float2* twx;         // [nx] exp(-2 pi i k / nx)
-  const float2* twy;         // [ny]
+  const float2* twx;         // stage twiddles of the x transform in thread order (twiddle_order)
+  const float2* twy;         // same for the y transform
   const float4* anchor;      // [n_ch][2][nx] FP32 hi + lo of exp(i dz (K - k)) / (nx ny g_x)
   const float* gcorr;        // [n_ch][2][nx] -dz / (2 K)
-  const float2* qy;          // [ny] {qy^2, 1/g_y - 1} at y-spectrum positions
+  const float2* qy;          // [16][ny/16] {qy^2, 1/g_y - 1}: entry k T + t is position 16 t + k
   int nx, ny, z;
 };
 

@@ -58,8 +58,9 @@ typedef struct bpm_plan_s* bpm_plan;
 
 /* Transverse grid and march.  dims = 2: (x, z), ny must be 1; dims = 3: (x, y, z).
  * nx (and ny) are powers of two: 256..8192 for dims = 2, 64..1024 for dims = 3.
- * split_order: 1 (first-order splitting a1 = b1 = 1 of Eq. split-op; the only
- * order implemented).  zassenhaus: 1 applies exp(D2 dz-hat^2/2),
+ * split_order (Eq. split-op): 1 = first order (a1 = b1 = 1, Eq. fov4); 2 = Strang
+ * (a = (0, 1), b = (1/2, 1/2): half coupling, propagation, half coupling, both
+ * halves with Pi and u sampled at z_n; dims = 2 only).  zassenhaus: 1 applies exp(D2 dz-hat^2/2),
  * D2 = (chi_h/2/cos alpha)^2, to the zeroth Jacobi-Anger term (Section 2,
  * equation after Eq. split-op); 0 leaves it out. */
 typedef struct {

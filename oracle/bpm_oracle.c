@@ -54,7 +54,7 @@ typedef struct {
   double dx, dy, dz;
   double chi0_re, chi0_im, chih_re, chih_im, chihb_re, chihb_im;
   double theta_B, lambda_B, x_surface, thickness;
-  int32_t zassenhaus, reserved;
+  int32_t zassenhaus, split_order; /* split_order 1: Eq. fov4; 2: Strang (a = (0,1), b = (1/2,1/2)) */
   double theta_i, x0, w0, zx, zR;
 } orc_problem;
 
@@ -174,7 +174,15 @@ static double wavenumber_h(const orc_problem* p) {
   return 4.0 * ORC_PI * sin(p->theta_B) / p->lambda_B;
 }
 
+/* Coefficients of the susceptibility step B(frac dz) of Eq. split-op for one
+ * channel: the step length dz-hat is frac * k dz in Eqs. fov9, fov11, fov12. */
+static int chan_setup_frac(const orc_problem* p, double omega, double frac, orc_chan* c);
+
 static int chan_setup(const orc_problem* p, double omega, orc_chan* c) {
+  return chan_setup_frac(p, omega, 1.0, c);
+}
+
+static int chan_setup_frac(const orc_problem* p, double omega, double frac, orc_chan* c) {
   double k = omega / ORC_C_LIGHT;
   double h = wavenumber_h(p);
   double s = h / (2.0 * k);
@@ -183,7 +191,7 @@ static int chan_setup(const orc_problem* p, double omega, orc_chan* c) {
   cplx chi0 = p->chi0_re + I * p->chi0_im;
   cplx chih = p->chih_re + I * p->chih_im;
   cplx chihb = p->chihb_re + I * p->chihb_im;
-  double kdz = k * p->dz; /* normalised step dz-hat */
+  double kdz = frac * k * p->dz; /* normalised (fractional) step dz-hat */
   /* Eq. fov9 with delta-eps = chi0 + chihb e^{+ihx} + chih e^{-ihx}: the   */
   /* Jacobi-Anger argument is w = dz-hat sqrt(chih chihb)/cos(alpha), the    */
   /* constant part gives exp(i dz-hat chi0 / (2 cos alpha)).                  */
@@ -317,6 +325,17 @@ int orc_incident(const orc_problem* p, double omega, const double* S, cplx* e0, 
   return 0;
 }
 
+/* Pointwise two-beam coupling of Eq. fov10 in crystal cells, simultaneous update. */
+static void coupling_step(const orc_chan* c, const cplx* cf, const uint8_t* mk, cplx* e0, cplx* eh,
+                          size_t n) {
+  for (size_t i = 0; i < n; ++i) {
+    if (!mk[i]) continue;
+    cplx ap = e0[i], am = eh[i];
+    e0[i] = c->a * ap + c->bp * cf[i] * am;
+    eh[i] = c->a * am + c->bm * conj(cf[i]) * ap;
+  }
+}
+
 /* Split-step z-march of Eq. fov10 for one channel, steps z_begin ..        */
 /* z_begin+n_steps-1, fields e0/eh ([ny][nx]) advanced in place.              */
 /* Step n: A+- <- IFFT(FFT(A+-) p+-), then in crystal cells                   */
@@ -325,8 +344,11 @@ int orc_incident(const orc_problem* p, double omega, const double* S, cplx* e0, 
 int orc_march(const orc_problem* p, const double* u, double omega, int z_begin, int n_steps,
               cplx* e0, cplx* eh) {
   orc_chan c;
-  int rc = chan_setup(p, omega, &c);
+  int strang = (p->split_order == 2);
+  /* Strang: B(dz/2) A(dz) B(dz/2), both half steps with Pi and u at z_n */
+  int rc = chan_setup_frac(p, omega, strang ? 0.5 : 1.0, &c);
   if (rc) return rc;
+  if (p->split_order != 0 && p->split_order != 1 && p->split_order != 2) return 4;
   int ny = (p->dims == 3) ? p->ny : 1;
   size_t n = (size_t)p->nx * ny;
   cplx* pp = (cplx*)malloc(sizeof(cplx) * n);
@@ -347,6 +369,8 @@ int orc_march(const orc_problem* p, const double* u, double omega, int z_begin, 
       rc = 3;
       break;
     }
+    orc_deformation(p, u, zn, cf, mk);
+    if (strang) coupling_step(&c, cf, mk, e0, eh, n);
     orc_fft2(e0, p->nx, ny, -1);
     orc_fft2(eh, p->nx, ny, -1);
     for (size_t i = 0; i < n; ++i) {
@@ -355,13 +379,7 @@ int orc_march(const orc_problem* p, const double* u, double omega, int z_begin, 
     }
     orc_fft2(e0, p->nx, ny, +1);
     orc_fft2(eh, p->nx, ny, +1);
-    orc_deformation(p, u, zn, cf, mk);
-    for (size_t i = 0; i < n; ++i) {
-      if (!mk[i]) continue;
-      cplx ap = e0[i], am = eh[i];
-      e0[i] = c.a * ap + c.bp * cf[i] * am;
-      eh[i] = c.a * am + c.bm * conj(cf[i]) * ap;
-    }
+    coupling_step(&c, cf, mk, e0, eh, n);
   }
   free(pp);
   free(pm);

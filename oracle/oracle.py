@@ -62,7 +62,7 @@ class Problem(ctypes.Structure):
         ("chihb_re", ctypes.c_double), ("chihb_im", ctypes.c_double),
         ("theta_B", ctypes.c_double), ("lambda_B", ctypes.c_double),
         ("x_surface", ctypes.c_double), ("thickness", ctypes.c_double),
-        ("zassenhaus", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("zassenhaus", ctypes.c_int32), ("split_order", ctypes.c_int32),
         ("theta_i", ctypes.c_double), ("x0", ctypes.c_double), ("w0", ctypes.c_double),
         ("zx", ctypes.c_double), ("zR", ctypes.c_double),
     ]
@@ -114,7 +114,7 @@ def problem(w) -> Problem:
         complex(w.chih).real, complex(w.chih).imag,
         complex(w.chihb).real, complex(w.chihb).imag,
         float(w.theta_B), float(w.lambda_B), float(w.x_surface), float(w.thickness),
-        int(w.zassenhaus), 0,
+        int(w.zassenhaus), int(getattr(w, "split_order", 1)),
         float(w.theta_i), float(w.x0), float(w.w0), float(w.zx), float(w.zR),
     )
 

@@ -260,7 +260,7 @@ def plan_from_workload(w, stream=None, u=None) -> Plan:
     """Create a plan and load the crystal and the pulse of a workload record.
     u overrides w.u (e.g. with a device tensor)."""
     p = Plan(w.dims, w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.n_ch, stream=stream,
-             zassenhaus=w.zassenhaus)
+             zassenhaus=w.zassenhaus, split_order=getattr(w, "split_order", 1))
     p.set_crystal(w.chi0, w.chih, w.chihb, w.theta_B, w.lambda_B, w.x_surface, w.thickness,
                   u=w.u if u is None else u)
     p.set_pulse(w.omega, w.S, w.theta_i, w.x0, w.w0, w.zx, w.zR)

@@ -333,8 +333,10 @@ BPM_API bpm_status bpm_plan_create(const bpm_grid* grid, int n_channels, void* c
   if (n_channels < 1) return fail(nullptr, BPM_ERR_INVALID_ARG, "n_channels must be >= 1");
   if (g.nz < 1 || !(g.dx > 0) || !(g.dz > 0))
     return fail(nullptr, BPM_ERR_INVALID_ARG, "nz, dx and dz must be positive");
-  if (g.split_order != 1)
-    return fail(nullptr, BPM_ERR_UNSUPPORTED, "only first-order splitting is implemented");
+  if (g.split_order != 1 && g.split_order != 2)
+    return fail(nullptr, BPM_ERR_UNSUPPORTED, "split_order must be 1 or 2");
+  if (g.split_order == 2 && g.dims != 2)
+    return fail(nullptr, BPM_ERR_UNSUPPORTED, "Strang splitting is implemented for 2D plans");
   if (g.dims == 2) {
     if (g.ny != 1) return fail(nullptr, BPM_ERR_INVALID_ARG, "dims = 2 requires ny = 1");
     if (!is_pow2(g.nx) || g.nx < 256 || g.nx > 8192)
@@ -471,6 +473,7 @@ BPM_API bpm_status bpm_set_crystal(bpm_plan p, double chi0_re, double chi0_im, d
   sa.chihb_re = chihbar_re;
   sa.chihb_im = chihbar_im;
   sa.zassenhaus = p->grid.zassenhaus ? 1 : 0;
+  sa.coupling_frac = p->grid.split_order == 2 ? 0.5 : 1.0;
   sa.x_surface = x_surface;
   sa.x_end = x_surface + thickness;
   const size_t cells = size_t(p->grid.nz) * p->plane;
@@ -571,6 +574,7 @@ BPM_API bpm_status bpm_run(bpm_plan p, int n_steps) {
   a.n_ch = p->n_ch;
   a.z0 = p->z;
   a.n_steps = n_steps;
+  a.pre_couple = p->grid.split_order == 2 ? 1 : 0;
   int launches = 0, march_launches = 0;
   if (p->timing) BPM_CUDA(p, cudaEventRecord(p->ev0, p->stream), "timing event");
   if (p->grid.dims == 2) {
@@ -741,7 +745,7 @@ struct RoundSlot {
   BatchItem* h_items = nullptr;
   MarchArgs* d_plans = nullptr;
   BatchItem* d_items = nullptr;
-  int* d_counter = nullptr;  // [2]: small and big queue counters
+  int* d_counter = nullptr;  // [4]: one counter per queue
   int cap_plans = 0, cap_items = 0;
   cudaEvent_t free_ev = nullptr;  // recorded after the round's kernels
   bool used = false;
@@ -800,7 +804,7 @@ cudaError_t slot_reserve(RoundSlot& r, int n_plans, int n_items) {
     if ((e = cudaMallocHost(&r.h_items, sizeof(BatchItem) * r.cap_items)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&r.d_items, sizeof(BatchItem) * r.cap_items)) != cudaSuccess) return e;
   }
-  if (!r.d_counter && (e = cudaMalloc(&r.d_counter, 2 * sizeof(int))) != cudaSuccess) return e;
+  if (!r.d_counter && (e = cudaMalloc(&r.d_counter, 4 * sizeof(int))) != cudaSuccess) return e;
   if (!r.free_ev && (e = cudaEventCreateWithFlags(&r.free_ev, cudaEventDisableTiming)) != cudaSuccess)
     return e;
   return cudaSuccess;
@@ -830,6 +834,7 @@ MarchArgs march_args(bpm_plan p, int n_steps) {
   a.n_ch = p->n_ch;
   a.z0 = p->z;
   a.n_steps = n_steps;
+  a.pre_couple = p->grid.split_order == 2 ? 1 : 0;
   return a;
 }
 
@@ -843,10 +848,11 @@ bpm_status enqueue_round(bpm_batch b, RoundSlot& r, int chunk) {
     if (!e.finishing && !e.cancelled && e.plan->z < e.plan->grid.nz) act.push_back(i);
   }
   if (act.empty()) return BPM_OK;
+  // four queues: (Nx = 8192 or not) x (Strang or first order), each sorted longest first
   struct Tmp {
     BatchItem it;
     double cost;
-    bool big;
+    int q;
   };
   std::vector<Tmp> tmp;
   std::vector<int> steps(act.size());
@@ -855,39 +861,41 @@ bpm_status enqueue_round(bpm_batch b, RoundSlot& r, int chunk) {
     const int n = p->grid.nx;
     steps[k] = std::min(chunk, p->grid.nz - p->z);
     const int G = batch_group(n);
+    const int q = (n == 8192 ? 0 : 2) + (p->grid.split_order == 2 ? 0 : 1);
     for (int c0 = 0; c0 < p->n_ch; c0 += G) {
       Tmp t;
       t.it = BatchItem{k, c0, n, 0};
       t.cost = double(steps[k]) * n * std::min(G, p->n_ch - c0) * std::log2(double(n));
-      t.big = (n == 8192);
+      t.q = q;
       tmp.push_back(t);
     }
   }
-  std::stable_sort(tmp.begin(), tmp.end(), [](const Tmp& x, const Tmp& y) { return x.cost > y.cost; });
-  int n_small = 0, n_big = 0;
-  for (auto& t : tmp) (t.big ? n_big : n_small)++;
+  std::stable_sort(tmp.begin(), tmp.end(), [](const Tmp& x, const Tmp& y) {
+    return x.q != y.q ? x.q < y.q : x.cost > y.cost;
+  });
+  int cnt[4] = {0, 0, 0, 0};
+  for (auto& t : tmp) cnt[t.q]++;
   BPM_BCUDA(b, slot_reserve(r, int(act.size()), int(tmp.size())), "batch staging");
   if (r.used) BPM_BCUDA(b, cudaEventSynchronize(r.free_ev), "staging reuse");
   for (int k = 0; k < int(act.size()); ++k) r.h_plans[k] = march_args(b->entries[act[k]].plan, steps[k]);
-  int is = 0, ib = n_small;
-  for (auto& t : tmp) r.h_items[t.big ? ib++ : is++] = t.it;
+  for (size_t i = 0; i < tmp.size(); ++i) r.h_items[i] = tmp[i].it;
   const DeviceInfo& di = device_info();
   BPM_BCUDA(b, cudaMemcpyAsync(r.d_plans, r.h_plans, sizeof(MarchArgs) * act.size(),
                                cudaMemcpyHostToDevice, b->stream), "upload round");
   BPM_BCUDA(b, cudaMemcpyAsync(r.d_items, r.h_items, sizeof(BatchItem) * tmp.size(),
                                cudaMemcpyHostToDevice, b->stream), "upload items");
-  BPM_BCUDA(b, cudaMemsetAsync(r.d_counter, 0, 2 * sizeof(int), b->stream), "clear queue");
-  // The Nx = 8192 queue (the longest items) runs first on every SM, then the
-  // queue of smaller items on every SM: longest-processing-time-first across
-  // both queues, with an idle tail of at most one item per queue.
-  if (n_big > 0)
-    BPM_BCUDA(b, launch_batch(r.d_plans, r.d_items + n_small, n_big, r.d_counter + 1, true,
-                              std::min(n_big, di.sm_count), b->stream),
-              "batch kernel (Nx 8192)");
-  if (n_small > 0)
-    BPM_BCUDA(b, launch_batch(r.d_plans, r.d_items, n_small, r.d_counter, false,
-                              std::min(n_small, di.sm_count), b->stream),
-              "batch kernel");
+  BPM_BCUDA(b, cudaMemsetAsync(r.d_counter, 0, 4 * sizeof(int), b->stream), "clear queues");
+  // Queues run back to back, each on every SM: the Nx = 8192 items (the
+  // longest) first, then the smaller ones; the idle tail is one item per queue.
+  int off = 0;
+  for (int q = 0; q < 4; ++q) {
+    if (cnt[q] > 0)
+      BPM_BCUDA(b, launch_batch(r.d_plans, r.d_items + off, cnt[q], r.d_counter + q, q < 2,
+                                (q % 2) == 0, std::min(cnt[q], di.sm_count), b->stream),
+                "batch kernel");
+    off += cnt[q];
+  }
+  const int n_small = cnt[2] + cnt[3], n_big = cnt[0] + cnt[1];
   BPM_BCUDA(b, cudaEventRecord(r.free_ev, b->stream), "round event");
   r.used = true;
   b->last_items[0] = n_small;

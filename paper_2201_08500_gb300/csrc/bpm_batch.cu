@@ -30,6 +30,7 @@ constexpr size_t kSmallSmem =
     cmax(cmax(cmax(item_smem<256>(), item_smem<512>()), cmax(item_smem<1024>(), item_smem<2048>())),
          item_smem<4096>());
 
+template <bool STRANG>
 __global__ void __launch_bounds__(kSmallThreads, 1)
     batch_kernel(const MarchArgs* __restrict__ plans, const BatchItem* __restrict__ items,
                  int n_items, int* counter) {
@@ -44,16 +45,17 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
     const BatchItem item = items[it];
     const MarchArgs& A = plans[item.plan];
     switch (item.n) {
-      case 256: Resident<256, 16>::run_item(A, item.ch0, smem); break;
-      case 512: Resident<512, 8>::run_item(A, item.ch0, smem); break;
-      case 1024: Resident<1024, 4>::run_item(A, item.ch0, smem); break;
-      case 2048: Resident<2048, 2>::run_item(A, item.ch0, smem); break;
-      case 4096: Resident<4096, 1>::run_item(A, item.ch0, smem); break;
+      case 256: Resident<256, 16, STRANG>::run_item(A, item.ch0, smem); break;
+      case 512: Resident<512, 8, STRANG>::run_item(A, item.ch0, smem); break;
+      case 1024: Resident<1024, 4, STRANG>::run_item(A, item.ch0, smem); break;
+      case 2048: Resident<2048, 2, STRANG>::run_item(A, item.ch0, smem); break;
+      case 4096: Resident<4096, 1, STRANG>::run_item(A, item.ch0, smem); break;
       default: break;
     }
   }
 }
 
+template <bool STRANG>
 __global__ void __launch_bounds__(512, 1)
     batch_kernel_8192(const MarchArgs* __restrict__ plans, const BatchItem* __restrict__ items,
                       int n_items, int* counter) {
@@ -66,7 +68,7 @@ __global__ void __launch_bounds__(512, 1)
     const int it = s_item;
     if (it >= n_items) break;
     const BatchItem item = items[it];
-    if (item.n == 8192) Resident<8192, 1>::run_item(plans[item.plan], item.ch0, smem);
+    if (item.n == 8192) Resident<8192, 1, STRANG>::run_item(plans[item.plan], item.ch0, smem);
   }
 }
 
@@ -75,22 +77,30 @@ __global__ void __launch_bounds__(512, 1)
 int batch_group(int n) { return n == 8192 ? 1 : kSmallThreads / (n / 16); }
 
 cudaError_t launch_batch(const MarchArgs* plans, const BatchItem* items, int n_items, int* counter,
-                         bool big, int blocks, cudaStream_t s) {
+                         bool big, bool strang, int blocks, cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
-  if (!big)
-    batch_kernel<<<blocks, kSmallThreads, kSmallSmem, s>>>(plans, items, n_items, counter);
+  const size_t big_smem = Resident<8192, 1>::smem_bytes();
+  if (!big && !strang)
+    batch_kernel<false><<<blocks, kSmallThreads, kSmallSmem, s>>>(plans, items, n_items, counter);
+  else if (!big)
+    batch_kernel<true><<<blocks, kSmallThreads, kSmallSmem, s>>>(plans, items, n_items, counter);
+  else if (!strang)
+    batch_kernel_8192<false><<<blocks, 512, big_smem, s>>>(plans, items, n_items, counter);
   else
-    batch_kernel_8192<<<blocks, 512, Resident<8192, 1>::smem_bytes(), s>>>(plans, items, n_items,
-                                                                           counter);
+    batch_kernel_8192<true><<<blocks, 512, big_smem, s>>>(plans, items, n_items, counter);
   return cudaGetLastError();
 }
 
 cudaError_t batch_set_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       int(kSmallSmem));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(batch_kernel_8192, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(Resident<8192, 1>::smem_bytes()));
+  const int small = int(kSmallSmem), big = int(Resident<8192, 1>::smem_bytes());
+  cudaError_t r[] = {
+      cudaFuncSetAttribute(batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, small),
+      cudaFuncSetAttribute(batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, small),
+      cudaFuncSetAttribute(batch_kernel_8192<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big),
+      cudaFuncSetAttribute(batch_kernel_8192<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)};
+  for (cudaError_t e : r)
+    if (e != cudaSuccess) return e;
+  return cudaSuccess;
 }
 
 }  // namespace bpm

@@ -33,6 +33,7 @@ struct MarchArgs {
   int n_ch;
   int z0;
   int n_steps;
+  int pre_couple;            // 1: Strang splitting, a half coupling before each propagation
 };
 
 // Arguments of the 3D row / column passes (bpm_3d.cu).
@@ -58,6 +59,7 @@ struct SetupArgs {
   double h;                  // reciprocal-lattice vector
   double chi0_re, chi0_im, chih_re, chih_im, chihb_re, chihb_im;
   int zassenhaus;
+  double coupling_frac;      // fraction of dz per coupling application (Strang: 1/2)
   double x_surface, x_end;   // slab [x_surface, x_end)
   double theta_i, x0, w0, zx, zR;
 };
@@ -73,7 +75,7 @@ struct BatchItem {
 // Work-queue launchers (bpm_batch.cu).  big selects the Nx = 8192 kernel.
 int batch_group(int n);
 cudaError_t launch_batch(const MarchArgs* plans, const BatchItem* items, int n_items, int* counter,
-                         bool big, int blocks, cudaStream_t s);
+                         bool big, bool strang, int blocks, cudaStream_t s);
 
 // Host runtime helpers (bpm_api.cu): FFT constants of size n (twiddles, spectrum
 // order, round-trip gain; host memory owned by a process-wide cache) and a
@@ -92,6 +94,8 @@ int march_threads_per_channel(int n);
 int march_max_group(int n);
 size_t march_smem_bytes(int n, int group);
 cudaError_t launch_march(int n, int group, int blocks, const MarchArgs& a, cudaStream_t s);
+cudaError_t launch_march_strang(int n, int group, int blocks, const MarchArgs& a, cudaStream_t s);
+cudaError_t march_set_attributes_strang();
 
 // 3D passes (bpm_3d.cu).  mode: 0 forward x only, 1 inverse x + coupling +
 // forward x, 2 inverse x + coupling.

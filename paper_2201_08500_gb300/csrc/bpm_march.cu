@@ -17,29 +17,11 @@
 // reflectivity / transmissivity sums are reduced in FP64.
 #include <cuda_runtime.h>
 
-#include "bpm_resident.cuh"
+#include "bpm_march_impl.cuh"
 
 namespace bpm {
 
 namespace {
-
-template <int N, int G>
-__global__ void __launch_bounds__((N / 16) * G, 1) march_kernel(MarchArgs A) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  Resident<N, G>::run(A, smem);
-}
-
-template <int N, int G>
-cudaError_t launch_one(int blocks, const MarchArgs& a, cudaStream_t s) {
-  march_kernel<N, G><<<blocks, (N / 16) * G, Resident<N, G>::smem_bytes(), s>>>(a);
-  return cudaGetLastError();
-}
-
-template <int N, int G>
-cudaError_t attr_one() {
-  return cudaFuncSetAttribute(march_kernel<N, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(Resident<N, G>::smem_bytes()));
-}
 
 }  // namespace
 
@@ -68,19 +50,21 @@ size_t march_smem_bytes(int n, int group) {
 }
 
 cudaError_t march_set_attributes() {
-  cudaError_t e = cudaSuccess;
-  cudaError_t r[] = {attr_one<256, 1>(),  attr_one<256, 16>(), attr_one<512, 1>(),
-                     attr_one<512, 8>(),  attr_one<1024, 1>(), attr_one<1024, 4>(),
-                     attr_one<2048, 1>(), attr_one<2048, 2>(), attr_one<4096, 1>(),
-                     attr_one<8192, 1>()};
+  cudaError_t e = march_set_attributes_strang();
+  cudaError_t r[] = {attr_one<256, 1, false>(),  attr_one<256, 16, false>(),
+                     attr_one<512, 1, false>(),  attr_one<512, 8, false>(),
+                     attr_one<1024, 1, false>(), attr_one<1024, 4, false>(),
+                     attr_one<2048, 1, false>(), attr_one<2048, 2, false>(),
+                     attr_one<4096, 1, false>(), attr_one<8192, 1, false>()};
   for (cudaError_t x : r)
     if (x != cudaSuccess) e = x;
   return e;
 }
 
 cudaError_t launch_march(int n, int group, int blocks, const MarchArgs& a, cudaStream_t s) {
+  if (a.pre_couple) return launch_march_strang(n, group, blocks, a, s);
 #define BPM_LAUNCH_CASE(NN, GG) \
-  if (n == NN && group == GG) return launch_one<NN, GG>(blocks, a, s);
+  if (n == NN && group == GG) return launch_one<NN, GG, false>(blocks, a, s);
   BPM_LAUNCH_CASE(256, 1) BPM_LAUNCH_CASE(256, 16)
   BPM_LAUNCH_CASE(512, 1) BPM_LAUNCH_CASE(512, 8)
   BPM_LAUNCH_CASE(1024, 1) BPM_LAUNCH_CASE(1024, 4)

@@ -1,0 +1,32 @@
+// Single-plan launch wrappers of the resident march kernel, shared by the
+// first-order (bpm_march.cu) and Strang (bpm_march_strang.cu) translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "bpm_resident.cuh"
+
+namespace bpm {
+namespace {
+
+template <int N, int G, bool STRANG>
+__global__ void __launch_bounds__((N / 16) * G, 1) march_kernel(MarchArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Resident<N, G, STRANG>::run(A, smem);
+}
+
+template <int N, int G, bool STRANG>
+cudaError_t launch_one(int blocks, const MarchArgs& a, cudaStream_t s) {
+  march_kernel<N, G, STRANG><<<blocks, (N / 16) * G, Resident<N, G, STRANG>::smem_bytes(), s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int N, int G, bool STRANG>
+cudaError_t attr_one() {
+  return cudaFuncSetAttribute(march_kernel<N, G, STRANG>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(Resident<N, G, STRANG>::smem_bytes()));
+}
+
+}  // namespace
+}  // namespace bpm

@@ -23,7 +23,7 @@ BPM_DEV void group_sync(int g) {
   }
 }
 
-template <int N, int G>
+template <int N, int G, bool STRANG = false>
 struct Resident {
   using Gm = Geom<N>;
   static constexpr int T = Gm::T;
@@ -205,6 +205,10 @@ struct Resident {
       float2 c[16];
 #pragma unroll
       for (int k = 0; k < 16; ++k) c[k] = __ldg(crow + t + T * k);
+      if constexpr (STRANG) {  // B(dz/2) A(dz) B(dz/2), half-step coefficients in cf
+#pragma unroll
+        for (int k = 0; k < 16; ++k) couple(a[k], b[k], c[k], cf);
+      }
 
       fft_fwd(a, b, buf, twr, A.twiddle, t, g);
 #pragma unroll

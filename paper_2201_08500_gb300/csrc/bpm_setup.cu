@@ -152,7 +152,7 @@ __global__ void tables_kernel(SetupArgs sa, const double* __restrict__ omega,
   }
   const double cos_a = sqrt(1.0 - s_ratio * s_ratio);  // cos(alpha), Eq. fov3
   const double kdz = k * sa.dz;
-  if (threadIdx.x == 0) coef[ch] = channel_coef(sa, kdz, cos_a);
+  if (threadIdx.x == 0) coef[ch] = channel_coef(sa, kdz * sa.coupling_frac, cos_a);
   float4* out = tables + size_t(ch) * 2 * n;
   for (int p = threadIdx.x; p < n; p += blockDim.x) {
     const double q = qbin(rev[p], n, sa.dx);
@@ -182,7 +182,7 @@ __global__ void tables3d_kernel(SetupArgs sa, const double* __restrict__ omega,
   const double half_h = 0.5 * sa.h;
   const double s_ratio = half_h / k;
   const double cos_a = sqrt(1.0 - s_ratio * s_ratio);
-  if (threadIdx.x == 0) coef[ch] = channel_coef(sa, k * sa.dz, cos_a);
+  if (threadIdx.x == 0) coef[ch] = channel_coef(sa, k * sa.dz * sa.coupling_frac, cos_a);
   for (int cs = threadIdx.x; cs < n; cs += blockDim.x) {
     const int px = 16 * (cs % T) + cs / T;
     const double qx = qbin(revx[px], n, sa.dx);

@@ -61,6 +61,7 @@ class Workload:
     zR: float = 1.0
     zassenhaus: int = 1
     meta: dict = field(default_factory=dict)
+    split_order: int = 1  # 1: first-order splitting; 2: Strang
 
     @property
     def n_ch(self) -> int:

@@ -170,3 +170,19 @@ def test_graph_replay_equals_eager(stream):
     for p in plans:
         p.close()
     b.close()
+
+
+def test_strang_plans_in_a_mixed_batch(stream):
+    ws = mix(seed=17)[:3]
+    ws[1].split_order = 2
+    ref = [single(w, stream) for w in ws]
+    b = bpm.Batch(stream=stream)
+    plans = [bpm.plan_from_workload(w, stream=stream) for w in ws]
+    for p in plans:
+        b.submit(p)
+    b.run()
+    b.sync()
+    for p, r in zip(plans, ref):
+        assert_same(fetch(p), r)
+        p.close()
+    b.close()

@@ -187,3 +187,16 @@ def test_deformed_full_size_sampled_channels(stream):
     R = g["refl"][0]
     assert np.max(np.abs(R[pick] - e["oR"])) < 1e-5
     assert np.all(np.isfinite(g["e0"])) and np.all(np.isfinite(g["eh"]))
+
+
+@pytest.mark.parametrize("nx", [512, 4096])
+def test_strang_splitting_matches_oracle(stream, nx):
+    """Second-order splitting (Eq. split-op with a = (0, 1), b = (1/2, 1/2))."""
+    w = deformed_small(nx, nz=140, n_ch=3, seed=nx + 1)
+    w.split_order = 2
+    g = run_gpu(w, stream)
+    e = errors(w, g)
+    assert e["per_ch"] < TOL_FIELD and e["relh"] < TOL_FIELD, e
+    w1 = deformed_small(nx, nz=140, n_ch=3, seed=nx + 1)
+    g1 = run_gpu(w1, stream)
+    assert np.linalg.norm(g1["eh"] - g["eh"]) > 1e-4 * np.linalg.norm(g["eh"])  # a different scheme

@@ -433,3 +433,25 @@ def test_incident_beam_at_distance_equals_propagated_waist(dims):
     # the propagator is exact, the closed form paraxial: they differ by ~1/(k W0)^2
     assert 1 / (k * w0) ** 2 < 2e-8
     assert np.max(np.abs(e0 - far)) < 5e-8
+
+
+def test_strang_splitting_converges_at_second_order():
+    """Eq. split-op: first-order splitting (a1 = b1 = 1) converges as dz and the
+    Strang form (a = (0, 1), b = (1/2, 1/2)) as dz^2, to the same limit (finite
+    tilted beam in an unbounded crystal, where diffraction and coupling do not
+    commute)."""
+    Z = 40e-6
+
+    def run(order, nz):
+        w = make(nx=256, nz=nz, dz=Z / nz, x_surface=-1.0, thickness=2.0, x0=64 * 0.5e-6,
+                 w0=6 * 0.5e-6, chih=complex(-4e-6, 0), chihb=complex(-4e-6, 0),
+                 split_order=order)
+        e0, eh, init = orc.run(w, n_threads=1)
+        return np.concatenate([e0[0], eh[0]]), np.linalg.norm(init)
+
+    ref, n0 = run(2, 2560)
+    e1 = [np.linalg.norm(run(1, n)[0] - ref) / n0 for n in (40, 80, 160)]
+    e2 = [np.linalg.norm(run(2, n)[0] - ref) / n0 for n in (40, 80, 160)]
+    assert 1.8 < e1[1] / e1[2] < 2.4 and 1.8 < e1[0] / e1[1] < 2.6
+    assert 3.7 < e2[1] / e2[2] < 4.3 and 3.6 < e2[0] / e2[1] < 4.4
+    assert e2[2] < e1[2] / 5

@@ -94,6 +94,16 @@ BPM_API bpm_status bpm_set_crystal(bpm_plan plan, double chi0_re, double chi0_im
                                    double theta_B, double lambda_B, double x_surface,
                                    double thickness, const double* u_field, int u_on_device);
 
+/* Crystal shape beyond the symmetric-Bragg slab (the method sets the
+ * reflection geometry through the crystal's boundaries, end of Section 2):
+ * the entrance surface becomes x = x_surface + z tan_psi (asymmetric Bragg cut,
+ * the back surface parallel at thickness along x), and the crystal is cut to
+ * z_begin <= z < z_end (with an x range covering the grid this is a symmetric
+ * Laue slab).  Pi(x_j, z_n) uses x_j = j dx, z_n = n dz, half-open intervals.
+ * Call before or after bpm_set_crystal (the deformation factor is rebuilt).
+ * Defaults: tan_psi = 0, unbounded z.  Errors: INVALID_ARG, CUDA. */
+BPM_API bpm_status bpm_set_geometry(bpm_plan plan, double tan_psi, double z_begin, double z_end);
+
 /* Incident pulse (Section 3.1 beam, Eq. ref:tdp and the frequency decomposition
  * after it): omega[n_channels] angular frequencies (rad/s, uniformly spaced for
  * the time assembly), weight_re_im[2*n_channels] complex spectral amplitudes

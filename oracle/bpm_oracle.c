@@ -56,6 +56,11 @@ typedef struct {
   double theta_B, lambda_B, x_surface, thickness;
   int32_t zassenhaus, split_order; /* split_order 1: Eq. fov4; 2: Strang (a = (0,1), b = (1/2,1/2)) */
   double theta_i, x0, w0, zx, zR;
+  /* crystal shape (geometries by the crystal's boundaries, Section 2 end):
+   * entrance surface x = x_surface + z tan_psi (asymmetric cut), slab
+   * thickness along x, and the crystal cut to z_begin <= z < z_end (Laue slab
+   * when the x range is unbounded). */
+  double tan_psi, z_begin, z_end;
 } orc_problem;
 
 /* ------------------------------------------------------------------------- */
@@ -264,12 +269,19 @@ int orc_channel(const orc_problem* p, double omega, double* out_scalars, cplx* c
   return 0;
 }
 
-/* Crystal mask Pi(x) of a symmetric-Bragg slab (surfaces normal to x):     */
-/* 1 iff x_surface <= x_j < x_surface + thickness, x_j = j dx.               */
-static int inside(const orc_problem* p, int j) {
+/* Crystal mask Pi(x_j, z_n): x_j = j dx, z_n = n dz,                         */
+/*   x_surface + z tan_psi <= x_j < x_surface + z tan_psi + thickness           */
+/*   and z_begin <= z_n < z_end.                                               */
+/* tan_psi = 0 and an unbounded z range give the symmetric-Bragg slab.          */
+static int inside(const orc_problem* p, int j, int n) {
   double x = (double)j * p->dx;
-  double x_end = p->x_surface + p->thickness;
-  return (x >= p->x_surface) && (x < x_end);
+  double z = (double)n * p->dz;
+  if (!(z >= p->z_begin && z < p->z_end)) return 0;
+  double shift = z * p->tan_psi;
+  double lo = p->x_surface + shift;
+  double hi = p->x_surface + p->thickness;
+  hi = hi + shift;
+  return (x >= lo) && (x < hi);
 }
 
 /* Deformation factor c(x, z_n) = exp(+i h u(x, z_n)) (Eq. Authier, n=+1);   */
@@ -281,7 +293,7 @@ int orc_deformation(const orc_problem* p, const double* u, int z_index, cplx* c_
   for (int r = 0; r < ny; ++r)
     for (int j = 0; j < p->nx; ++j) {
       size_t idx = (size_t)r * p->nx + j;
-      int in = inside(p, j);
+      int in = inside(p, j, z_index);
       cplx cv = 0;
       if (in) {
         double uu = u ? u[((size_t)z_index * ny + r) * p->nx + j] : 0.0;

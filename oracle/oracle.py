@@ -46,7 +46,9 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", SRC, "-o", tmp, "-lm"]
+    # no FMA contraction: mask decisions and phases round the same way on every host
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-pthread", SRC,
+           "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB
@@ -65,6 +67,7 @@ class Problem(ctypes.Structure):
         ("zassenhaus", ctypes.c_int32), ("split_order", ctypes.c_int32),
         ("theta_i", ctypes.c_double), ("x0", ctypes.c_double), ("w0", ctypes.c_double),
         ("zx", ctypes.c_double), ("zR", ctypes.c_double),
+        ("tan_psi", ctypes.c_double), ("z_begin", ctypes.c_double), ("z_end", ctypes.c_double),
     ]
 
 
@@ -116,6 +119,8 @@ def problem(w) -> Problem:
         float(w.theta_B), float(w.lambda_B), float(w.x_surface), float(w.thickness),
         int(w.zassenhaus), int(getattr(w, "split_order", 1)),
         float(w.theta_i), float(w.x0), float(w.w0), float(w.zx), float(w.zR),
+        float(getattr(w, "tan_psi", 0.0)), float(getattr(w, "z_begin", -np.inf)),
+        float(getattr(w, "z_end", np.inf)),
     )
 
 

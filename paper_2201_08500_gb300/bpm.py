@@ -26,7 +26,7 @@ EXPORTS = ("bpm_plan_create", "bpm_set_crystal", "bpm_set_pulse", "bpm_set_field
            "bpm_batch_create", "bpm_batch_submit", "bpm_batch_step", "bpm_batch_run",
            "bpm_batch_run_graph", "bpm_batch_poll", "bpm_batch_cancel", "bpm_batch_sync",
            "bpm_batch_info", "bpm_batch_last_error", "bpm_batch_destroy", "bpm_run_noalloc",
-           "bpm_noalloc_scratch_bytes", "bpm_noalloc_last_error", "bpm_set_stream")
+           "bpm_noalloc_scratch_bytes", "bpm_noalloc_last_error", "bpm_set_stream", "bpm_set_geometry")
 
 
 class BpmError(RuntimeError):
@@ -82,6 +82,7 @@ def load(path: str = LIB_PATH):
         "bpm_run": ([_P, _I], _I),
         "bpm_sync": ([_P], _I),
         "bpm_set_stream": ([_P, _P], _I),
+        "bpm_set_geometry": ([_P, _D, _D, _D], _I),
         "bpm_fetch_fields": ([_P, _I, _P, ctypes.c_size_t, _I], _I),
         "bpm_fetch_reflectivity": ([_P, _P, _P, _P], _I),
         "bpm_set_timing": ([_P, _I], _I),
@@ -196,6 +197,10 @@ class Plan:
         if _is_device(u):
             self._keep = [u]
 
+    def set_geometry(self, tan_psi=0.0, z_begin=-np.inf, z_end=np.inf):
+        self._check(self._L.bpm_set_geometry(self._h, float(tan_psi), float(z_begin),
+                                             float(z_end)))
+
     def set_pulse(self, omega, S, theta_i, x0, w0, zx=0.0, zR=1.0):
         omega = np.ascontiguousarray(omega, dtype=np.float64)
         S = np.ascontiguousarray(S, dtype=np.complex128)
@@ -261,6 +266,9 @@ def plan_from_workload(w, stream=None, u=None) -> Plan:
     u overrides w.u (e.g. with a device tensor)."""
     p = Plan(w.dims, w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.n_ch, stream=stream,
              zassenhaus=w.zassenhaus, split_order=getattr(w, "split_order", 1))
+    geo = (getattr(w, "tan_psi", 0.0), getattr(w, "z_begin", -np.inf), getattr(w, "z_end", np.inf))
+    if geo != (0.0, -np.inf, np.inf):
+        p.set_geometry(*geo)
     p.set_crystal(w.chi0, w.chih, w.chihb, w.theta_B, w.lambda_B, w.x_surface, w.thickness,
                   u=w.u if u is None else u)
     p.set_pulse(w.omega, w.S, w.theta_i, w.x0, w.w0, w.zx, w.zR)

@@ -200,7 +200,7 @@ struct bpm_plan_s {
   std::string err = "no error";
   int plane = 0;
 
-  bool have_crystal = false, have_pulse = false, time_valid = false;
+  bool have_crystal = false, have_pulse = false, time_valid = false, have_geometry = false;
   int z = 0;
   SetupArgs sa{};
   double domega = 1.0;
@@ -476,6 +476,11 @@ BPM_API bpm_status bpm_set_crystal(bpm_plan p, double chi0_re, double chi0_im, d
   sa.coupling_frac = p->grid.split_order == 2 ? 0.5 : 1.0;
   sa.x_surface = x_surface;
   sa.x_end = x_surface + thickness;
+  if (!p->have_geometry) {
+    sa.tan_psi = 0.0;
+    sa.z_begin = -HUGE_VAL;
+    sa.z_end = HUGE_VAL;
+  }
   const size_t cells = size_t(p->grid.nz) * p->plane;
   const double* u_dev = nullptr;
   if (u_field) {
@@ -497,6 +502,18 @@ BPM_API bpm_status bpm_set_crystal(bpm_plan p, double chi0_re, double chi0_im, d
   p->have_crystal = true;
   p->have_pulse = false;
   p->time_valid = false;
+  return BPM_OK;
+}
+
+BPM_API bpm_status bpm_set_geometry(bpm_plan p, double tan_psi, double z_begin, double z_end) {
+  if (!p) return fail(nullptr, BPM_ERR_INVALID_ARG, "null plan");
+  if (!(std::fabs(tan_psi) < 1e3) || !(z_begin < z_end))
+    return fail(p, BPM_ERR_INVALID_ARG, "need |tan_psi| < 1e3 and z_begin < z_end");
+  p->sa.tan_psi = tan_psi;
+  p->sa.z_begin = z_begin;
+  p->sa.z_end = z_end;
+  p->have_geometry = true;
+  if (p->have_crystal) BPM_CUDA(p, enqueue_crystal(p), "deformation kernel");
   return BPM_OK;
 }
 

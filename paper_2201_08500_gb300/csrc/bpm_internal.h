@@ -60,7 +60,9 @@ struct SetupArgs {
   double chi0_re, chi0_im, chih_re, chih_im, chihb_re, chihb_im;
   int zassenhaus;
   double coupling_frac;      // fraction of dz per coupling application (Strang: 1/2)
-  double x_surface, x_end;   // slab [x_surface, x_end)
+  double x_surface, x_end;   // slab [x_surface, x_end) at z = 0
+  double tan_psi;            // entrance surface x = x_surface + z tan_psi (asymmetric cut)
+  double z_begin, z_end;     // crystal only for z_begin <= z < z_end (Laue slab)
   double theta_i, x0, w0, zx, zR;
 };
 

@@ -77,14 +77,25 @@ __device__ __forceinline__ dc tilted_propagator(double k, double Q2, double dz) 
   return dc{m * c, m * s};
 }
 
+// Crystal mask Pi(x_j, z_n) (the crystal's boundaries set the geometry, end of
+// Section 2): x_surface + z tan_psi <= x_j < x_end + z tan_psi and
+// z_begin <= z_n < z_end, with x_j = j dx, z_n = n dz.  Every product and sum is
+// rounded explicitly (no contraction) so that the decision is reproducible.
+__device__ __forceinline__ bool in_crystal(const SetupArgs& sa, int j, int n) {
+  const double x = __dmul_rn(double(j), sa.dx);
+  const double z = __dmul_rn(double(n), sa.dz);
+  if (!(z >= sa.z_begin && z < sa.z_end)) return false;
+  const double shift = __dmul_rn(z, sa.tan_psi);
+  return x >= __dadd_rn(sa.x_surface, shift) && x < __dadd_rn(sa.x_end, shift);
+}
+
 __global__ void deformation_kernel(SetupArgs sa, const double* __restrict__ u, float2* cfield) {
   const long long plane = (long long)sa.nx * sa.ny;
   const long long total = plane * sa.nz;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const int j = int(i % sa.nx);
-    const double x = double(j) * sa.dx;
-    const bool in = (x >= sa.x_surface) && (x < sa.x_end);
+    const bool in = in_crystal(sa, j, int(i / plane));
     float2 c = make_float2(0.f, 0.f);
     if (in) {
       const double ph = u ? sa.h * u[i] : 0.0;

@@ -147,6 +147,9 @@ BPM_API bpm_status bpm_run_noalloc(const bpm_grid* grid, int n_channels,
   sa.coupling_frac = 1.0;
   sa.x_surface = crystal->x_surface;
   sa.x_end = crystal->x_surface + crystal->thickness;
+  sa.tan_psi = 0.0;  // symmetric-Bragg slab only on this entry point
+  sa.z_begin = -HUGE_VAL;
+  sa.z_end = HUGE_VAL;
   sa.theta_i = beam->theta_i;
   sa.x0 = beam->x0;
   sa.w0 = beam->w0;

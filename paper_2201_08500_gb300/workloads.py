@@ -62,6 +62,10 @@ class Workload:
     zassenhaus: int = 1
     meta: dict = field(default_factory=dict)
     split_order: int = 1  # 1: first-order splitting; 2: Strang
+    # crystal shape: entrance surface x = x_surface + z tan_psi, crystal in z_begin <= z < z_end
+    tan_psi: float = 0.0
+    z_begin: float = -math.inf
+    z_end: float = math.inf
 
     @property
     def n_ch(self) -> int:

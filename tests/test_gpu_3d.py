@@ -114,3 +114,11 @@ def test_3d_full_transverse_grid_sampled_channel():
 def test_3d_rejects_unsupported_sizes():
     with pytest.raises(bpm.BpmError):
         bpm.Plan(3, 2048, 256, 10, 1e-6, 1e-6, 1e-6, 1)
+
+
+def test_3d_asymmetric_cut_matches_oracle():
+    import math
+    w = case3d(256, 256, 30, 1, seed=11)
+    w.tan_psi = math.tan(math.radians(7.0))
+    e0, eh, _ = gpu(w)
+    check(w, e0, eh)

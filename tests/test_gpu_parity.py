@@ -200,3 +200,22 @@ def test_strang_splitting_matches_oracle(stream, nx):
     w1 = deformed_small(nx, nz=140, n_ch=3, seed=nx + 1)
     g1 = run_gpu(w1, stream)
     assert np.linalg.norm(g1["eh"] - g["eh"]) > 1e-4 * np.linalg.norm(g["eh"])  # a different scheme
+
+
+@pytest.mark.parametrize("psi_deg", [6.0, -10.0])
+def test_asymmetric_bragg_geometry_matches_oracle(stream, psi_deg):
+    import math
+    w = deformed_small(2048, nz=200, n_ch=3, seed=7)
+    w.tan_psi = math.tan(math.radians(psi_deg))
+    g = run_gpu(w, stream)
+    e = errors(w, g)
+    assert e["per_ch"] < TOL_FIELD and e["relh"] < TOL_FIELD, e
+
+
+def test_laue_slab_geometry_matches_oracle(stream):
+    w = deformed_small(1024, nz=220, n_ch=4, seed=8)
+    w.x_surface, w.thickness = -1.0, 2.0  # crystal across the whole x range ...
+    w.z_begin, w.z_end = 40.5 * w.dz, 170.5 * w.dz  # ... between two z planes
+    g = run_gpu(w, stream)
+    e = errors(w, g)
+    assert e["per_ch"] < TOL_FIELD and e["relh"] < TOL_FIELD, e

@@ -204,12 +204,16 @@ def test_flux_identity_with_and_without_zassenhaus(zass):
 
 
 # ----------------------------------------------------------------------------- P7 Bragg slab
-def slab_reflectivity(alpha, k, chi0, chih, chihb, d, sin_t):
-    """Textbook two-beam symmetric-Bragg plane-wave reflectivity for a slab of
-    thickness d (sigma polarisation): sin(t) D0' = (ik/2)(chi0 D0 + chihb Dh),
-    -sin(t) Dh' = (ik/2)(chih D0 + (chi0 - alpha) Dh), D0(0) = 1, Dh(d) = 0."""
-    c = 1j * k / (2 * sin_t)
-    M = np.array([[c * chi0, c * chihb], [-c * chih, -c * (chi0 - alpha)]])
+def slab_reflectivity(alpha, k, chi0, chih, chihb, d, sin_t, gamma_h=None):
+    """Textbook two-beam Bragg plane-wave amplitude reflectivity |Dh(0)|^2 for a
+    slab of thickness d along its inward normal (sigma polarisation):
+    gamma0 D0' = (ik/2)(chi0 D0 + chihb Dh), gammah Dh' = (ik/2)(chih D0 +
+    (chi0 - alpha) Dh), D0(0) = 1, Dh(d) = 0; gamma0 = sin_t and, for the
+    symmetric case, gammah = -sin_t."""
+    gh = -sin_t if gamma_h is None else gamma_h
+    c0 = 1j * k / (2 * sin_t)
+    ch = 1j * k / (2 * gh)
+    M = np.array([[c0 * chi0, c0 * chihb], [ch * chih, ch * (chi0 - alpha)]])
     lam, V = np.linalg.eig(M)
     # D(s) = c1 v1 e^{l1 s} + c2 v2 e^{l2 s}; scale each mode by its value at its own end
     e = np.exp(lam * d)
@@ -455,3 +459,60 @@ def test_strang_splitting_converges_at_second_order():
     assert 1.8 < e1[1] / e1[2] < 2.4 and 1.8 < e1[0] / e1[1] < 2.6
     assert 3.7 < e2[1] / e2[2] < 4.3 and 3.6 < e2[0] / e2[1] < 4.4
     assert e2[2] < e1[2] / 5
+
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("psi_deg", [8.0, -8.0])
+def test_asymmetric_bragg_matches_textbook_curve(psi_deg):
+    """Asymmetric Bragg cut (entrance surface tilted by psi from the reflecting
+    planes, set only through the crystal mask as the paper describes): the
+    reflected power equals the textbook asymmetric two-beam result, direction
+    cosines gamma0 = sin(theta_B - psi), gammah = -sin(theta_B + psi), thickness
+    d cos(psi) along the normal and flux factor |gammah/gamma0|."""
+    dx = 0.5e-6
+    nx, nz = 4096, 1800
+    psi = math.radians(psi_deg)
+    g0 = math.sin(THETA_B - psi)
+    gh = -math.sin(THETA_B + psi)
+    s2 = math.sin(THETA_B) ** 2
+    eps_d = abs(CHIH) / s2
+    eps_c = -CHI0.real / (2 * s2)
+    eps = eps_c + eps_d * np.array([-1.5, -0.6, 0.0, 0.5, 1.0, 2.0])
+    omega = omega_bragg() * (1 + eps)
+    w0, d_cells = 200 * dx, 100
+    w = make(nx=nx, nz=nz, dx=dx, dz=dx, x_surface=1999.5 * dx, thickness=d_cells * dx,
+             x0=1000 * dx, w0=w0, omega=omega, S=np.ones(omega.size, complex),
+             tan_psi=math.tan(psi))
+    e0, eh, init = orc.run(w)
+    R_bpm, _ = orc.reflectivity(init, e0, eh)
+    h = h_of(w)
+    m = np.arange(nx)
+    q = 2 * math.pi * np.where(m < nx // 2, m, m - nx) / (nx * dx)
+    for i, om in enumerate(omega):
+        k = om / C_LIGHT
+        dq = k * math.sin(THETA_B) - h / 2
+        wgt = np.exp(-((q - dq) ** 2) * w0 ** 2 / 2)
+        sel = wgt > 1e-12 * wgt.max()
+        Rq = np.array([slab_reflectivity(-2 * h * qq / k ** 2, k, CHI0, CHIH, CHIH,
+                                         d_cells * dx * math.cos(psi), g0, gamma_h=gh)
+                       for qq in q[sel]])
+        R_tb = abs(gh / g0) * np.sum(wgt[sel] * Rq) / np.sum(wgt[sel])
+        assert abs(R_bpm[i] - R_tb) < 8e-3, (psi_deg, i, R_bpm[i], R_tb)
+
+
+def test_laue_slab_pendelloesung():
+    """Symmetric Laue slab (crystal only for z_begin <= z < z_end, all x): a
+    plane wave at the Bragg condition leaves with |A-|^2/|A+(0)|^2 =
+    sin^2(pi t / Lambda0), t the slab thickness along z."""
+    chih = complex(-4e-6, 0.0)
+    dz = 0.1e-6
+    lam = LAMBDA_B
+    L0 = lam * math.cos(THETA_B) / abs(chih)
+    for na, nb in ((30, 90), (10, 150)):
+        w = make(chi0=0j, chih=chih, chihb=chih, nx=64, nz=200, dz=dz, x_surface=-1.0,
+                 thickness=2.0, w0=1e6, x0=0.0, z_begin=(na - 0.5) * dz, z_end=(nb - 0.5) * dz)
+        e0, eh, init = orc.run(w, n_threads=1)
+        t = (nb - na) * dz
+        ratio = np.mean(np.abs(eh[0]) ** 2) / np.mean(np.abs(init[0]) ** 2)
+        assert abs(ratio - math.sin(math.pi * t / L0) ** 2) < 1e-3

@@ -216,7 +216,7 @@ def run_batched(args, world, rank, local):
                   "form": "per instance: setup kernels, one march launch, time response"},
         "speedup_vs_plain": ms_plain / ms_batched,
         "items": info["last_items"], "clocks": clocks,
-        "gpu_launches": None,
+        "gpu_launches": b.graph_kernels() * args.steps,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -294,8 +294,11 @@ def run_3d(args, world, rank, local):
 def run_served(args, world, rank, local):
     """Poisson stream of requests (80 % single-channel rocking-curve probes
     Nx = 512 / 300 steps, 20 % instances drawn from the uneven batch), offered at
-    `load` x the measured capacity of the batched executor; served form
-    (continuous batching) vs plain form (one request at a time)."""
+    `load` x the measured capacity of the batched executor.  Three forms on the
+    same arrivals: served with a short-request lane (4 SMs) beside the long
+    lane, served with one lane, and plain (one request at a time).  Then the
+    first quarter of the requests again as a burst (all arriving at once):
+    served vs plain throughput at saturation."""
     import torch
     from paper_2201_08500_gb300 import bpm, serve
 
@@ -331,21 +334,35 @@ def run_served(args, world, rank, local):
     rate = args.load * capacity / mean_cost
     arr = serve.poisson_arrivals(len(reqs_w), rate, 4 + rank)
 
-    def make():
-        return [serve.Request(i, w, u, float(a))
-                for i, (w, u, a) in enumerate(zip(reqs_w, reqs_u, arr))]
+    def make(n=None, burst=False):
+        n = len(reqs_w) if n is None else n
+        return [serve.Request(i, w, u, 0.0 if burst else float(a))
+                for i, (w, u, a) in enumerate(zip(reqs_w[:n], reqs_u[:n], arr[:n]))]
+
+    def served_form(reqs, short_sms):
+        srv = serve.Server(hbm_budget_bytes=96 * 2 ** 30, chunk=256, keep_fields=False,
+                           short_sms=short_sms)
+        srv.serve(reqs)
+        st = serve.summarize(reqs)
+        st["rounds"], st["slots"] = srv.rounds, srv.n_slots
+        srv.close()
+        return st
 
     served = make()
-    srv = serve.Server(hbm_budget_bytes=96 * 2 ** 30, chunk=256, keep_fields=False)
-    srv.serve(served)
-    s_stats = serve.summarize(served)
-    s_stats["rounds"] = srv.rounds
-    s_stats["slots"] = srv.n_slots
-    srv.close()
+    s_stats = served_form(served, 4)
+    one = make()
+    o_stats = served_form(one, 0)
     plain = make()
     serve.serve_plain(plain, keep_fields=False)
     p_stats = serve.summarize(plain)
-    same = all(np.array_equal(a.R, c.R) for a, c in zip(served, plain))
+    same = all(np.array_equal(a.R, c.R) and np.array_equal(a.R, d.R)
+               for a, c, d in zip(served, plain, one))
+    n_burst = max(1, len(reqs_w) // 4)
+    sb = make(n_burst, burst=True)
+    sb_stats = served_form(sb, 4)
+    pb = make(n_burst, burst=True)
+    serve.serve_plain(pb, keep_fields=False)
+    pb_stats = serve.summarize(pb)
     line = {
         "metric": METRIC + " served vs plain; p50/p99 latency", "value": s_stats["throughput"],
         "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": 1,
@@ -353,10 +370,13 @@ def run_served(args, world, rank, local):
         "vs_baseline": None, "dtype": "c64 fields / f32 butterflies", "data": "synthetic",
         "config": {"workload": f"Poisson stream of {len(served)} requests (80 % probes Nx=512 "
                                f"Nz=300 1 channel, 20 % uneven-batch instances), offered load "
-                               f"{args.load} x capacity {capacity:.3e} cell-updates/s",
-                   "rate_per_s": rate, "chunk_steps": 256, "hbm_budget_gb": 96},
-        "served": s_stats, "plain": p_stats,
-        "served_vs_plain_throughput": s_stats["throughput"] / p_stats["throughput"],
+                               f"{args.load} x capacity {capacity:.3e} cell-updates/s; burst: "
+                               f"the first {n_burst} requests all at t = 0",
+                   "rate_per_s": rate, "chunk_steps": 256, "hbm_budget_gb": 96,
+                   "short_lane_sms": 4},
+        "served": s_stats, "served_one_lane": o_stats, "plain": p_stats,
+        "burst": {"served": sb_stats, "plain": pb_stats,
+                  "served_vs_plain_throughput": sb_stats["throughput"] / pb_stats["throughput"]},
         "results_equal_alone_vs_mix": same,
     }
     if rank == 0:

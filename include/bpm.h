@@ -234,6 +234,10 @@ BPM_API bpm_status bpm_batch_run(bpm_batch b);
  * set of plans changes, replayed otherwise.  Asynchronous. */
 BPM_API bpm_status bpm_batch_run_graph(bpm_batch b);
 
+/* Kernel launches in one replay of the graph bpm_batch_run_graph captured
+ * (0 before the first capture).  Errors: INVALID_ARG. */
+BPM_API bpm_status bpm_batch_graph_kernels(bpm_batch b, int* kernels);
+
 /* Non-blocking completion test of a ticket; done = 1 once its results can be
  * fetched from its plan (the plan's budget share is then released).
  * Errors: CANCELLED, INVALID_ARG (unknown ticket), CUDA. */
@@ -245,6 +249,18 @@ BPM_API bpm_status bpm_batch_cancel(bpm_batch b, uint64_t ticket);
 
 /* Waits for all enqueued rounds. */
 BPM_API bpm_status bpm_batch_sync(bpm_batch b);
+
+/* Number of enqueued rounds whose kernels have not finished (0..3).  A step
+ * while 3 rounds are in flight waits for the oldest on the host; a driver that
+ * must not block (a server feeding several batches) steps only below 3.
+ * Errors: INVALID_ARG, CUDA (a round's kernels failed). */
+BPM_API bpm_status bpm_batch_pending(bpm_batch b, int* rounds_in_flight);
+
+/* Caps the persistent launches of later rounds at max_blocks blocks (one per
+ * SM; <= 0 restores every SM).  Two batches on different streams with caps
+ * that add up to the SM count run side by side, e.g. a lane for short requests
+ * next to a lane for long ones.  Errors: INVALID_ARG. */
+BPM_API bpm_status bpm_batch_set_max_blocks(bpm_batch b, int max_blocks);
 
 /* Admitted unfinished plans, their bytes, rounds enqueued so far and the item
  * counts [small, Nx = 8192] of the last round (any pointer may be NULL). */

@@ -26,7 +26,9 @@ EXPORTS = ("bpm_plan_create", "bpm_set_crystal", "bpm_set_pulse", "bpm_set_field
            "bpm_batch_create", "bpm_batch_submit", "bpm_batch_step", "bpm_batch_run",
            "bpm_batch_run_graph", "bpm_batch_poll", "bpm_batch_cancel", "bpm_batch_sync",
            "bpm_batch_info", "bpm_batch_last_error", "bpm_batch_destroy", "bpm_run_noalloc",
-           "bpm_noalloc_scratch_bytes", "bpm_noalloc_last_error", "bpm_set_stream", "bpm_set_geometry")
+           "bpm_noalloc_scratch_bytes", "bpm_noalloc_last_error", "bpm_set_stream",
+           "bpm_set_geometry", "bpm_batch_set_max_blocks", "bpm_batch_pending",
+           "bpm_batch_graph_kernels")
 
 
 class BpmError(RuntimeError):
@@ -83,6 +85,9 @@ def load(path: str = LIB_PATH):
         "bpm_sync": ([_P], _I),
         "bpm_set_stream": ([_P, _P], _I),
         "bpm_set_geometry": ([_P, _D, _D, _D], _I),
+        "bpm_batch_set_max_blocks": ([_P, _I], _I),
+        "bpm_batch_pending": ([_P, ctypes.POINTER(ctypes.c_int)], _I),
+        "bpm_batch_graph_kernels": ([_P, ctypes.POINTER(ctypes.c_int)], _I),
         "bpm_fetch_fields": ([_P, _I, _P, ctypes.c_size_t, _I], _I),
         "bpm_fetch_reflectivity": ([_P, _P, _P, _P], _I),
         "bpm_set_timing": ([_P, _I], _I),
@@ -318,6 +323,21 @@ class Batch:
 
     def run(self):
         self._check(self._L.bpm_batch_run(self._h))
+
+    def set_max_blocks(self, n: int):
+        self._check(self._L.bpm_batch_set_max_blocks(self._h, int(n)))
+
+    def graph_kernels(self) -> int:
+        """Kernel launches in one replay of the captured graph."""
+        n = ctypes.c_int(0)
+        self._check(self._L.bpm_batch_graph_kernels(self._h, ctypes.byref(n)))
+        return n.value
+
+    def pending(self) -> int:
+        """Rounds enqueued whose kernels have not finished yet."""
+        n = ctypes.c_int(0)
+        self._check(self._L.bpm_batch_pending(self._h, ctypes.byref(n)))
+        return n.value
 
     def run_graph(self):
         self._check(self._L.bpm_batch_run_graph(self._h))

@@ -396,8 +396,13 @@ BPM_API bpm_status bpm_plan_create(const bpm_grid* grid, int n_channels, void* c
     return st;
   }
   const FftConsts& fc = fft_consts(g.nx);
-  check(cudaMemcpyAsync(p->twiddle, fc.tw.data(), sizeof(float2) * g.nx, cudaMemcpyHostToDevice,
-                        p->stream),
+  // Nx = 8192 reads its stage twiddles from memory in thread order (coalesced);
+  // smaller sizes load them into registers from the natural table.
+  const std::vector<float2> tw_ord = (g.dims == 2 && g.nx == 8192) ? twiddle_order(g.nx)
+                                                                   : std::vector<float2>();
+  check(cudaMemcpyAsync(p->twiddle, tw_ord.empty() ? fc.tw.data() : tw_ord.data(),
+                        sizeof(float2) * (tw_ord.empty() ? size_t(g.nx) : tw_ord.size()),
+                        cudaMemcpyHostToDevice, p->stream),
         "upload twiddles");
   check(cudaMemcpyAsync(p->rev, fc.rev.data(), sizeof(int) * g.nx, cudaMemcpyHostToDevice,
                         p->stream),
@@ -787,6 +792,8 @@ struct bpm_batch_s {
   std::string err = "no error";
   int rounds = 0;
   int last_items[2] = {0, 0};
+  int max_blocks = 0;  // SM cap of the persistent launches (0: every SM)
+  int graph_kernels = 0;  // kernel nodes of the captured graph
 };
 
 namespace {
@@ -805,19 +812,22 @@ bpm_status bfail(bpm_batch b, bpm_status s, const std::string& msg) {
                    std::string(what) + ": " + cudaGetErrorString(e_));                 \
   } while (0)
 
+// Growing a slot frees its old buffers, which synchronizes the device; the
+// first reservation is sized (256 plans, 16384 items: ~0.3 MB) so that a
+// server's rounds never grow one.
 cudaError_t slot_reserve(RoundSlot& r, int n_plans, int n_items) {
   cudaError_t e = cudaSuccess;
   if (n_plans > r.cap_plans) {
     if (r.h_plans) cudaFreeHost(r.h_plans);
     if (r.d_plans) cudaFree(r.d_plans);
-    r.cap_plans = n_plans * 2;
+    r.cap_plans = std::max(n_plans * 2, 256);
     if ((e = cudaMallocHost(&r.h_plans, sizeof(MarchArgs) * r.cap_plans)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&r.d_plans, sizeof(MarchArgs) * r.cap_plans)) != cudaSuccess) return e;
   }
   if (n_items > r.cap_items) {
     if (r.h_items) cudaFreeHost(r.h_items);
     if (r.d_items) cudaFree(r.d_items);
-    r.cap_items = n_items * 2;
+    r.cap_items = std::max(n_items * 2, 16384);
     if ((e = cudaMallocHost(&r.h_items, sizeof(BatchItem) * r.cap_items)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&r.d_items, sizeof(BatchItem) * r.cap_items)) != cudaSuccess) return e;
   }
@@ -897,6 +907,7 @@ bpm_status enqueue_round(bpm_batch b, RoundSlot& r, int chunk) {
   for (int k = 0; k < int(act.size()); ++k) r.h_plans[k] = march_args(b->entries[act[k]].plan, steps[k]);
   for (size_t i = 0; i < tmp.size(); ++i) r.h_items[i] = tmp[i].it;
   const DeviceInfo& di = device_info();
+  const int sms = b->max_blocks > 0 ? std::min(b->max_blocks, di.sm_count) : di.sm_count;
   BPM_BCUDA(b, cudaMemcpyAsync(r.d_plans, r.h_plans, sizeof(MarchArgs) * act.size(),
                                cudaMemcpyHostToDevice, b->stream), "upload round");
   BPM_BCUDA(b, cudaMemcpyAsync(r.d_items, r.h_items, sizeof(BatchItem) * tmp.size(),
@@ -908,7 +919,7 @@ bpm_status enqueue_round(bpm_batch b, RoundSlot& r, int chunk) {
   for (int q = 0; q < 4; ++q) {
     if (cnt[q] > 0)
       BPM_BCUDA(b, launch_batch(r.d_plans, r.d_items + off, cnt[q], r.d_counter + q, q < 2,
-                                (q % 2) == 0, std::min(cnt[q], di.sm_count), b->stream),
+                                (q % 2) == 0, std::min(cnt[q], sms), b->stream),
                 "batch kernel");
     off += cnt[q];
   }
@@ -1104,6 +1115,16 @@ BPM_API bpm_status bpm_batch_run_graph(bpm_batch b) {
       return st;
     }
     BPM_BCUDA(b, ce, "end capture");
+    size_t n_nodes = 0;
+    BPM_BCUDA(b, cudaGraphGetNodes(g, nullptr, &n_nodes), "graph nodes");
+    std::vector<cudaGraphNode_t> nodes(n_nodes);
+    BPM_BCUDA(b, cudaGraphGetNodes(g, nodes.data(), &n_nodes), "graph nodes");
+    b->graph_kernels = 0;
+    for (cudaGraphNode_t nd : nodes) {
+      cudaGraphNodeType ty;
+      BPM_BCUDA(b, cudaGraphNodeGetType(nd, &ty), "graph node type");
+      if (ty == cudaGraphNodeTypeKernel) ++b->graph_kernels;
+    }
     cudaError_t ie = cudaGraphInstantiate(&b->graph, g, 0);
     cudaGraphDestroy(g);
     BPM_BCUDA(b, ie, "graph instantiate");
@@ -1115,6 +1136,31 @@ BPM_API bpm_status bpm_batch_run_graph(bpm_batch b) {
     e.plan->time_valid = true;
   }
   BPM_BCUDA(b, cudaGraphLaunch(b->graph, b->stream), "graph launch");
+  return BPM_OK;
+}
+
+BPM_API bpm_status bpm_batch_graph_kernels(bpm_batch b, int* kernels) {
+  if (!b || !kernels) return bfail(b, BPM_ERR_INVALID_ARG, "null argument");
+  *kernels = b->graph ? b->graph_kernels : 0;
+  return BPM_OK;
+}
+
+BPM_API bpm_status bpm_batch_pending(bpm_batch b, int* rounds_in_flight) {
+  if (!b || !rounds_in_flight) return bfail(b, BPM_ERR_INVALID_ARG, "null argument");
+  int n = 0;
+  for (const RoundSlot& r : b->slots) {
+    if (!r.used) continue;
+    const cudaError_t q = cudaEventQuery(r.free_ev);
+    if (q == cudaErrorNotReady) ++n;
+    else if (q != cudaSuccess) return bfail(b, BPM_ERR_CUDA, std::string("round: ") + cudaGetErrorString(q));
+  }
+  *rounds_in_flight = n;
+  return BPM_OK;
+}
+
+BPM_API bpm_status bpm_batch_set_max_blocks(bpm_batch b, int max_blocks) {
+  if (!b) return bfail(nullptr, BPM_ERR_INVALID_ARG, "null batch");
+  b->max_blocks = max_blocks > 0 ? max_blocks : 0;
   return BPM_OK;
 }
 

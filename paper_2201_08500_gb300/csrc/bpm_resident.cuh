@@ -39,6 +39,14 @@ struct Resident {
   __host__ __device__ static constexpr size_t slot_bytes() { return tab_bytes() + buf_bytes() + red_bytes(); }
   __host__ __device__ static constexpr size_t smem_bytes() { return G * slot_bytes(); }
 
+  // Offset of stage s in the thread-ordered twiddle table used when the
+  // twiddles do not stay in registers (N = 8192): stage s, output m and
+  // j = t % L(s+1) at tw[off(s) + (m - 1) L(s+1) + j], so that consecutive
+  // threads read adjacent entries.
+  __host__ __device__ static constexpr int tw_off(int s) {
+    return s == 0 ? 0 : tw_off(s - 1) + 15 * Gm::LN(s - 1);
+  }
+
   // Inter-stage twiddle of stage s for this thread and output m.
   template <int s>
   static BPM_DEV float2 twiddle(const float2 (&twr)[kTwSlots][15], const float2* tw, int t, int m) {
@@ -46,8 +54,7 @@ struct Resident {
       return twr[s][m - 1];
     } else {
       constexpr int ln = Gm::LN(s);
-      constexpr int stride = N / Gm::L(s);
-      return __ldg(tw + stride * (t % ln) * m);
+      return __ldg(tw + tw_off(s) + (m - 1) * ln + (t % ln));
     }
   }
 

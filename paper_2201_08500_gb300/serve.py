@@ -5,10 +5,14 @@ The served form:
   * admits a request when a plan slot of its shape is free, or when the device
     memory budget allows a new slot (plans are pooled by shape, so the steady
     state allocates nothing);
-  * sets its crystal and pulse on a setup stream (fields stay on the device);
-  * advances every admitted request by rounds of `chunk` z steps, each round
-    one persistent work-queue launch; requests admitted while earlier ones are
-    on the GPU join the next round, and slots free as requests complete;
+  * sends it to one of two lanes by size: short requests (single-channel
+    probes) to a lane on a few reserved SMs, the rest to a lane on the others;
+  * sets its crystal and pulse on the lane's setup stream (fields stay on the
+    device);
+  * advances every admitted request by rounds (long lane: `chunk` z steps;
+    short lane: to completion), each round one persistent work-queue launch
+    per queue; requests admitted while earlier ones are on the GPU join the
+    next round, and slots free as requests complete;
   * on completion copies the result (reflectivities and the reflected field)
     to the host and returns the slot.
 The plain form serves the same arrivals one request at a time with one march
@@ -46,23 +50,56 @@ def poisson_arrivals(n: int, rate: float, seed: int) -> np.ndarray:
     return np.cumsum(rng.exponential(1.0 / rate, size=n))
 
 
-class Server:
-    """Continuous batching over a bpm.Batch with plan slots pooled by shape."""
+class _Lane:
+    """One batch with its own stream, setup stream, SM cap and round length."""
 
-    def __init__(self, hbm_budget_bytes: int, chunk: int = 256, stream=None, keep_fields=True):
+    def __init__(self, torch, max_blocks: int, chunk: int, stream=None, priority: int = 0):
+        self.stream = stream if stream is not None else torch.cuda.Stream(priority=priority)
+        self.setup_stream = torch.cuda.Stream()
+        self.batch = bpm.Batch(hbm_budget_bytes=0, stream=self.stream)
+        if max_blocks > 0:
+            self.batch.set_max_blocks(max_blocks)
+        self.chunk = int(chunk)
+        self.active = {}   # ticket -> [req, plan, steps still to enqueue]
+        self.rounds = 0
+
+
+class Server:
+    """Continuous batching over bpm.Batch lanes with plan slots pooled by shape.
+
+    Requests of at most `short_cells` cell-updates (single-channel probes) go to
+    a short lane that owns `short_sms` SMs and runs each request to completion in
+    one round; everything else goes to the long lane (the other SMs, rounds of
+    `chunk` steps).  The persistent launches of the two lanes hold one block per
+    SM, so their blocks fit side by side and a probe does not wait behind a long
+    round; the short lane's stream has the higher priority, so that its blocks
+    are placed first when SMs free up.  short_sms = 0 gives one lane on every SM.
+    """
+
+    def __init__(self, hbm_budget_bytes: int, chunk: int = 256, stream=None, keep_fields=True,
+                 short_cells: float = 1e7, short_sms: int = 4):
         import torch
         self.torch = torch
-        self.stream = stream if stream is not None else torch.cuda.current_stream()
-        self.setup_stream = torch.cuda.Stream()
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
         self.budget = int(hbm_budget_bytes)
-        self.chunk = int(chunk)
-        self.batch = bpm.Batch(hbm_budget_bytes=0, stream=self.stream)
+        self.short_cells = float(short_cells) if short_sms > 0 else -1.0
+        self.long = _Lane(torch, sms - short_sms if short_sms > 0 else 0, chunk,
+                          stream if stream is not None else torch.cuda.current_stream())
+        # high priority: when a long kernel's blocks retire, waiting probe blocks go first
+        self.short = _Lane(torch, short_sms, 1 << 30, priority=-1) if short_sms > 0 else None
         self.pool = collections.defaultdict(list)  # shape -> free plans
         self.bytes_in_slots = 0
         self.keep_fields = keep_fields
         self.n_slots = 0
 
-    def _slot(self, w):
+    @property
+    def rounds(self):
+        return self.long.rounds + (self.short.rounds if self.short else 0)
+
+    def _lane(self, w):
+        return self.short if w.cell_updates <= self.short_cells else self.long
+
+    def _slot(self, w, lane):
         free = self.pool[shape_key(w)]
         if free:
             return free.pop()
@@ -70,7 +107,7 @@ class Server:
         if self.bytes_in_slots + need > self.budget:
             return None
         p = bpm.Plan(w.dims, w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.n_ch,
-                     stream=self.setup_stream, zassenhaus=w.zassenhaus)
+                     stream=lane.setup_stream, zassenhaus=w.zassenhaus)
         p.bytes = need
         self.bytes_in_slots += need
         self.n_slots += 1
@@ -86,43 +123,48 @@ class Server:
         """Run the arrival process in real time; fills done_at, R (and eh)."""
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         waiting = collections.deque()
-        active = {}   # ticket -> (req, plan, steps still to enqueue)
+        lanes = [lane for lane in (self.short, self.long) if lane is not None]
         t0 = time.perf_counter()
-        rounds = 0
-        while pending or waiting or active:
+        while pending or waiting or any(lane.active for lane in lanes):
             now = time.perf_counter() - t0
             while pending and pending[0].arrival <= now:
                 waiting.append(pending.popleft())
+            blocked = collections.deque()
             while waiting:
-                req = waiting[0]
-                p = self._slot(req.work)
+                req = waiting.popleft()
+                lane = self._lane(req.work)
+                p = self._slot(req.work, lane)
                 if p is None:
-                    break  # no memory for a new slot of this shape yet
+                    blocked.append(req)  # no memory for a new slot of this shape yet
+                    continue
                 self._load(p, req)
-                t = self.batch.submit(p)
-                active[t] = [req, p, req.work.nz]
-                waiting.popleft()
-            todo = [a for a in active.values() if a[2] > 0]
-            if todo:
-                self.batch.step(self.chunk)
-                rounds += 1
-                for a in todo:
-                    a[2] = max(0, a[2] - self.chunk)
-            else:
-                time.sleep(5e-5)
-            for t in list(active):
-                if self.batch.poll(t):
-                    req, p, _ = active.pop(t)
-                    req.R = p.reflectivity()[0]
-                    if self.keep_fields:
-                        req.eh = p.eh()
-                    req.done_at = time.perf_counter() - t0
-                    self.pool[shape_key(req.work)].append(p)
-            if not todo and not waiting and pending and not active:
-                dt = pending[0].arrival - (time.perf_counter() - t0)
+                t = lane.batch.submit(p)
+                lane.active[t] = [req, p, req.work.nz]
+            waiting = blocked
+            stepped = False
+            for lane in lanes:
+                todo = [a for a in lane.active.values() if a[2] > 0]
+                # keep at most two rounds in flight so that a step never blocks
+                if todo and lane.batch.pending() < 2:
+                    lane.batch.step(lane.chunk)
+                    lane.rounds += 1
+                    stepped = True
+                    for a in todo:
+                        a[2] = max(0, a[2] - lane.chunk)
+            for lane in lanes:
+                for t in list(lane.active):
+                    if lane.batch.poll(t):
+                        req, p, _ = lane.active.pop(t)
+                        req.R = p.reflectivity()[0]
+                        if self.keep_fields:
+                            req.eh = p.eh()
+                        req.done_at = time.perf_counter() - t0
+                        self.pool[shape_key(req.work)].append(p)
+            if not stepped:
+                idle = not waiting and not any(lane.active for lane in lanes)
+                dt = pending[0].arrival - (time.perf_counter() - t0) if (idle and pending) else 5e-5
                 if dt > 0:
                     time.sleep(min(dt, 0.01))
-        self.rounds = rounds
         return requests
 
     def close(self):
@@ -130,7 +172,9 @@ class Server:
             for p in plans:
                 p.close()
         self.pool.clear()
-        self.batch.close()
+        for lane in (self.short, self.long):
+            if lane is not None:
+                lane.batch.close()
 
 
 def serve_plain(requests, stream=None, keep_fields=True):
@@ -163,11 +207,22 @@ def serve_plain(requests, stream=None, keep_fields=True):
     return requests
 
 
-def summarize(requests) -> dict:
-    lat = np.array([r.done_at - r.arrival for r in requests])
+def summarize(requests, short_cells: float = 1e7) -> dict:
+    """Latency percentiles (all requests, and short / long ones apart) and
+    throughput in cell-updates per second over the makespan."""
+    def pct(rs):
+        if not rs:
+            return {}
+        lat = np.array([r.done_at - r.arrival for r in rs]) * 1e3
+        return {"n": len(rs), "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean())}
+
     cells = sum(r.work.cell_updates for r in requests)
     span = max(r.done_at for r in requests) - min(r.arrival for r in requests)
-    return {"requests": len(requests), "p50_ms": float(np.percentile(lat, 50) * 1e3),
-            "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
-            "makespan_s": float(span), "cell_updates": int(cells),
-            "throughput": float(cells / span)}
+    out = pct(requests)
+    out["requests"] = out.pop("n")
+    out.update({"makespan_s": float(span), "cell_updates": int(cells),
+                "throughput": float(cells / span),
+                "short": pct([r for r in requests if r.work.cell_updates <= short_cells]),
+                "long": pct([r for r in requests if r.work.cell_updates > short_cells])})
+    return out

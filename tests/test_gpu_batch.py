@@ -162,11 +162,14 @@ def test_graph_replay_equals_eager(stream):
     b = bpm.Batch(stream=stream)
     for p in plans:
         b.submit(p)
+    assert b.graph_kernels() == 0
     for _ in range(3):  # capture, then replay twice
         b.run_graph()
         b.sync()
         for p, r in zip(plans, ref):
             assert_same(fetch(p), r)
+    # per plan at least tables, incident field and time response; two march queues
+    assert b.graph_kernels() >= 3 * len(plans) + 2
     for p in plans:
         p.close()
     b.close()
@@ -183,6 +186,29 @@ def test_strang_plans_in_a_mixed_batch(stream):
     b.run()
     b.sync()
     for p, r in zip(plans, ref):
+        assert_same(fetch(p), r)
+        p.close()
+    b.close()
+
+
+def test_block_cap_and_rounds_in_flight(stream):
+    """A batch capped at 3 blocks gives the same fields; pending() counts rounds
+    whose kernels have not finished and is 0 after a sync."""
+    ws = mix(seed=8)[:3]
+    ref = [single(w, stream) for w in ws]
+    b = bpm.Batch(stream=stream)
+    b.set_max_blocks(3)
+    plans = [bpm.plan_from_workload(w, stream=stream) for w in ws]
+    tickets = [b.submit(p) for p in plans]
+    assert b.pending() == 0
+    for _ in range(3):
+        b.step(50)
+    assert 0 <= b.pending() <= 3
+    b.run()
+    b.sync()
+    assert b.pending() == 0
+    for t, p, r in zip(tickets, plans, ref):
+        assert b.poll(t)
         assert_same(fetch(p), r)
         p.close()
     b.close()

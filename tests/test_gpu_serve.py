@@ -36,14 +36,17 @@ def alone(req):
     return out
 
 
-@pytest.mark.parametrize("budget_gb", [64.0, 0.25])
-def test_served_results_equal_alone(budget_gb):
+@pytest.mark.parametrize("budget_gb,short_sms", [(64.0, 4), (0.25, 4), (64.0, 0)])
+def test_served_results_equal_alone(budget_gb, short_sms):
+    """Two lanes (probes on 4 reserved SMs) or one; generous or tight memory."""
     import torch
     torch.cuda.set_device(0)
     reqs = requests()
-    srv = serve.Server(hbm_budget_bytes=int(budget_gb * 2 ** 30), chunk=64)
+    # probes are 153,600 cell-updates, the four instances here 0.98M to 3.9M
+    srv = serve.Server(hbm_budget_bytes=int(budget_gb * 2 ** 30), chunk=64, short_sms=short_sms,
+                       short_cells=5e5)
     srv.serve(reqs)
-    stats = serve.summarize(reqs)
+    stats = serve.summarize(reqs, short_cells=5e5)
     srv.close()
     assert all(r.done_at >= r.arrival for r in reqs)
     assert stats["p99_ms"] >= stats["p50_ms"] > 0
@@ -53,6 +56,8 @@ def test_served_results_equal_alone(budget_gb):
         assert np.array_equal(r.eh, eh), r.work.name
     if budget_gb < 1:
         assert srv.n_slots < len(reqs)  # slots were reused under the tight budget
+    if short_sms:
+        assert stats["short"]["n"] == 30 and stats["long"]["n"] == 4
 
 
 def test_plain_server_matches_too():

@@ -112,6 +112,27 @@ def dist_env():
     return world, rank, local
 
 
+def rank_workload(n_ch: int, nx: int, nz: int, rank: int):
+    """Each rank marches its own instance of the same size (seed 2 + rank):
+    channels and instances are independent, so ranks exchange no data."""
+    return workloads.deformed(n_ch=n_ch, nx=nx, nz=nz, seed=2 + rank)
+
+
+def max_over_ranks(value: float, dist=None, device="cpu") -> float:
+    """The slowest rank's time (an all-reduce MAX of one number; identity at N = 1)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world: int, cells_per_rank: int, ms: float) -> float:
+    """Cell-updates of all ranks divided by the slowest rank's time."""
+    return world * cells_per_rank / (ms * 1e-3)
+
+
 def oracle_sample(w, n_channels: int, n_threads: int):
     """Time the FP64 oracle (as it stands) on n_channels channels of workload w."""
     import oracle.oracle as orc
@@ -427,7 +448,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    w = workloads.deformed(n_ch=args.channels, nx=args.nx, nz=args.nz, seed=2 + rank)
+    w = rank_workload(args.channels, args.nx, args.nz, rank)
     stream = torch.cuda.current_stream()
     u_dev = torch.from_numpy(np.ascontiguousarray(w.u)).cuda()
     plan = bpm.Plan(w.dims, w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.n_ch, stream=stream,
@@ -466,12 +487,9 @@ def main():
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms_local = sum(step_ms) / len(step_ms)
-    t = torch.tensor([ms_local], device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = max_over_ranks(ms_local, dist, device="cuda")
     cells_per_rank = w.cell_updates
-    value = world * cells_per_rank / (ms * 1e-3)
+    value = whole_job_value(world, cells_per_rank, ms)
 
     # end to end through the C ABI with host buffers: pinned u in, R and the
     # time response out, copies inside the timed region

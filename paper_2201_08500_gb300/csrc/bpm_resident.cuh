@@ -94,22 +94,26 @@ struct Resident {
     }
   }
 
-  // Move both envelopes from the layout of stage SF to that of stage ST.
+  // Move both envelopes from the layout of stage SF to that of stage ST.  The
+  // two envelopes of a position share one 16-byte slot {E0, Eh}, so each
+  // element costs one 128-bit store and one 128-bit load; with the XOR swizzle
+  // the 8 threads of every 128-bit access phase hit distinct bank groups for
+  // all sizes and stages.
   template <int SF, int ST>
   static BPM_DEV void exchange(float2 (&a)[16], float2 (&b)[16], float2* buf, int t, int g) {
+    float4* b4 = reinterpret_cast<float4*>(buf);
     group_sync<T, G>(g);
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
       const int p = swz(Gm::template pos<SF>(t, k));
-      buf[p] = a[k];
-      buf[N + p] = b[k];
+      b4[p] = make_float4(a[k].x, a[k].y, b[k].x, b[k].y);
     }
     group_sync<T, G>(g);
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
-      const int p = swz(Gm::template pos<ST>(t, k));
-      a[k] = buf[p];
-      b[k] = buf[N + p];
+      const float4 v = b4[swz(Gm::template pos<ST>(t, k))];
+      a[k] = make_float2(v.x, v.y);
+      b[k] = make_float2(v.z, v.w);
     }
   }
 
@@ -148,12 +152,9 @@ struct Resident {
     stage_inv<0>(a, b, twr, tw, t);
   }
 
-  // Pointwise two-beam coupling of Eq. fov10 at one cell.  c = 0 marks vacuum
-  // (a = 1, b = 0); inside the crystal |c| = 1.
-  static BPM_DEV void couple(float2& p, float2& m, float2 c, const ChannelCoef& cf) {
-    const bool in = (c.x != 0.f) || (c.y != 0.f);
-    const float ahx = in ? cf.a_hi.x : 1.f, ahy = in ? cf.a_hi.y : 0.f;
-    const float alx = in ? cf.a_lo.x : 0.f, aly = in ? cf.a_lo.y : 0.f;
+  // Pointwise two-beam coupling of Eq. fov10 at one crystal cell (|c| = 1).
+  static BPM_DEV void couple_in(float2& p, float2& m, float2 c, const ChannelCoef& cf) {
+    const float ahx = cf.a_hi.x, ahy = cf.a_hi.y, alx = cf.a_lo.x, aly = cf.a_lo.y;
     const float2 bpc = c_mul(cf.bp, c);   // b+ c
     const float2 bmc = c_mulc(cf.bm, c);  // b- conj(c)
     const float px = fmaf(ahx, p.x, fmaf(-ahy, p.y, fmaf(bpc.x, m.x, fmaf(-bpc.y, m.y,
@@ -166,6 +167,17 @@ struct Resident {
                                                                            fmaf(alx, m.y, aly * m.x)))));
     p = make_float2(px, py);
     m = make_float2(mx, my);
+  }
+
+  // Coupling of this thread's 16 cells.  c = 0 marks vacuum (Pi = 0), where the
+  // coupling is the identity (a = 1, b = 0) and nothing is computed.  Register
+  // k of a warp holds 32 consecutive x, so the test is warp-uniform except at
+  // the crystal's surfaces.
+  static BPM_DEV void couple_row(float2 (&a)[16], float2 (&b)[16], const float2 (&c)[16],
+                                 const ChannelCoef& cf) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if (c[k].x != 0.f || c[k].y != 0.f) couple_in(a[k], b[k], c[k], cf);
   }
 
   // Loads this thread's inter-stage twiddles (kept in registers for N <= 4096).
@@ -212,10 +224,7 @@ struct Resident {
       float2 c[16];
 #pragma unroll
       for (int k = 0; k < 16; ++k) c[k] = __ldg(crow + t + T * k);
-      if constexpr (STRANG) {  // B(dz/2) A(dz) B(dz/2), half-step coefficients in cf
-#pragma unroll
-        for (int k = 0; k < 16; ++k) couple(a[k], b[k], c[k], cf);
-      }
+      if constexpr (STRANG) couple_row(a, b, c, cf);  // B(dz/2) A(dz) B(dz/2), half-step cf
 
       fft_fwd(a, b, buf, twr, A.twiddle, t, g);
 #pragma unroll
@@ -232,8 +241,7 @@ struct Resident {
         b[k] = c_mul2(b[k], pb);
       }
       fft_inv(a, b, buf, twr, A.twiddle, t, g);
-#pragma unroll
-      for (int k = 0; k < 16; ++k) couple(a[k], b[k], c[k], cf);
+      couple_row(a, b, c, cf);
     }
 
     double sa = 0.0, sb = 0.0;

@@ -176,6 +176,60 @@ typedef struct {
 BPM_API bpm_status bpm_set_timing(bpm_plan plan, int enable);
 BPM_API bpm_status bpm_get_stats(bpm_plan plan, bpm_stats* out);
 
+/* ---------------------------------------------------------------------------
+ * Launch forms and their autotuner.  The paper has no counterpart: these
+ * choose how the same arithmetic is laid out on the GPU, never what it
+ * computes (every form gives bitwise the same fields).
+ *
+ *   form               2D march: 0 = propagator tables in shared memory and
+ *                      twiddles in registers, one channel group per SM;
+ *                      1 = tables and twiddles read from L2, at most 128
+ *                      registers, two channel groups per SM (first order,
+ *                      Nx <= 4096, channels_per_block = the size's maximum).
+ *   channels_per_block 2D march: 1, or the maximum of the size (16, 8, 4, 2, 1
+ *                      for Nx = 256, 512, 1024, 2048, >= 4096).
+ *   row_threads        3D row pass: 256 or 512 threads per block, i.e. a tile
+ *                      of 256/T or 512/T rows (T = nx/16); taller tiles move
+ *                      longer column segments in the transposed store.
+ *   ms                 bpm_tune: median time of `steps` steps in this form. */
+typedef struct {
+  int32_t form;
+  int32_t channels_per_block;
+  int32_t row_threads;
+  float ms;
+} bpm_launch;
+
+/* The plan's launch form (chosen at creation: the tuned form of its shape if
+ * bpm_tune or bpm_tune_load provided one, else the default).  Errors: INVALID_ARG. */
+BPM_API bpm_status bpm_get_launch(bpm_plan plan, bpm_launch* out);
+
+/* Forces a launch form for later bpm_run calls (ms is ignored).
+ * Errors: INVALID_ARG (a form this plan cannot run). */
+BPM_API bpm_status bpm_set_launch(bpm_plan plan, const bpm_launch* form);
+
+/* Autotuner: creates a scratch plan of this grid (nz replaced by `steps`) and
+ * n_channels, with a synthetic crystal slab over a quarter of x and a Gaussian
+ * beam, times every launch form the shape can run (one warm-up and three timed
+ * runs of `steps` steps each, CUDA events), and records the fastest for later
+ * plans of the same (dims, nx, ny, split_order, n_channels) in this process.
+ * best receives the fastest; all (capacity max_all, may be NULL) receives every
+ * measured form, and n_all their count.  Runs on its own stream and waits for it.
+ * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
+BPM_API bpm_status bpm_tune(const bpm_grid* grid, int n_channels, int steps, bpm_launch* best,
+                            bpm_launch* all, int max_all, int* n_all);
+
+/* Writes the tuned forms of this process to a text file, one shape per line,
+ * tagged with the device name and SM count.  Errors: INVALID_ARG (cannot write). */
+BPM_API bpm_status bpm_tune_save(const char* path);
+
+/* Adds the entries of a file written by bpm_tune_save whose device tag matches
+ * this GPU (others are skipped); malformed lines are an error.  n_loaded (may
+ * be NULL) receives the number of entries taken.  Errors: INVALID_ARG. */
+BPM_API bpm_status bpm_tune_load(const char* path, int* n_loaded);
+
+/* Forgets every tuned form of this process. */
+BPM_API void bpm_tune_clear(void);
+
 /* Message of the last failed call on this plan (plan = NULL: the last failed
  * bpm_plan_create / batch call of this thread).  Never NULL. */
 BPM_API const char* bpm_last_error(bpm_plan plan);

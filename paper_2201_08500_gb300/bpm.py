@@ -28,7 +28,8 @@ EXPORTS = ("bpm_plan_create", "bpm_set_crystal", "bpm_set_pulse", "bpm_set_field
            "bpm_batch_info", "bpm_batch_last_error", "bpm_batch_destroy", "bpm_run_noalloc",
            "bpm_noalloc_scratch_bytes", "bpm_noalloc_last_error", "bpm_set_stream",
            "bpm_set_geometry", "bpm_batch_set_max_blocks", "bpm_batch_pending",
-           "bpm_batch_graph_kernels")
+           "bpm_batch_graph_kernels", "bpm_get_launch", "bpm_set_launch", "bpm_tune",
+           "bpm_tune_save", "bpm_tune_load", "bpm_tune_clear")
 
 
 class BpmError(RuntimeError):
@@ -49,6 +50,15 @@ class Stats(ctypes.Structure):
                 ("march_launches", ctypes.c_int32), ("threads_per_channel", ctypes.c_int32),
                 ("channels_per_block", ctypes.c_int32), ("blocks", ctypes.c_int32),
                 ("smem_bytes", ctypes.c_int32)]
+
+
+class Launch(ctypes.Structure):
+    """Launch form of a plan (see bpm_launch in include/bpm.h)."""
+    _fields_ = [("form", ctypes.c_int32), ("channels_per_block", ctypes.c_int32),
+                ("row_threads", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class CrystalParams(ctypes.Structure):
@@ -88,6 +98,13 @@ def load(path: str = LIB_PATH):
         "bpm_batch_set_max_blocks": ([_P, _I], _I),
         "bpm_batch_pending": ([_P, ctypes.POINTER(ctypes.c_int)], _I),
         "bpm_batch_graph_kernels": ([_P, ctypes.POINTER(ctypes.c_int)], _I),
+        "bpm_get_launch": ([_P, ctypes.POINTER(Launch)], _I),
+        "bpm_set_launch": ([_P, ctypes.POINTER(Launch)], _I),
+        "bpm_tune": ([ctypes.POINTER(Grid), _I, _I, ctypes.POINTER(Launch), ctypes.POINTER(Launch),
+                      _I, ctypes.POINTER(_I)], _I),
+        "bpm_tune_save": ([ctypes.c_char_p], _I),
+        "bpm_tune_load": ([ctypes.c_char_p, ctypes.POINTER(_I)], _I),
+        "bpm_tune_clear": ([], None),
         "bpm_fetch_fields": ([_P, _I, _P, ctypes.c_size_t, _I], _I),
         "bpm_fetch_reflectivity": ([_P, _P, _P, _P], _I),
         "bpm_set_timing": ([_P, _I], _I),
@@ -264,6 +281,58 @@ class Plan:
         s = Stats()
         self._check(self._L.bpm_get_stats(self._h, ctypes.byref(s)))
         return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+    def launch(self) -> dict:
+        """The plan's launch form (form, channels_per_block, row_threads)."""
+        f = Launch()
+        self._check(self._L.bpm_get_launch(self._h, ctypes.byref(f)))
+        d = f.as_dict()
+        d.pop("ms")
+        return d
+
+    def set_launch(self, form=None, channels_per_block=None, row_threads=None):
+        """Force a launch form for later runs (unspecified fields keep their value)."""
+        cur = self.launch()
+        f = Launch(int(cur["form"] if form is None else form),
+                   int(cur["channels_per_block"] if channels_per_block is None
+                       else channels_per_block),
+                   int(cur["row_threads"] if row_threads is None else row_threads), 0.0)
+        self._check(self._L.bpm_set_launch(self._h, ctypes.byref(f)))
+
+
+def tune(dims, nx, ny, dx, dy, dz, n_channels, split_order=1, zassenhaus=1, steps=16):
+    """Autotune the launch form of a plan shape (C++ tuner, see bpm_tune): times
+    every form on a scratch plan and keeps the fastest for later plans of this
+    shape.  Returns (best, all) as dicts with the median time in ms."""
+    L = load()
+    g = Grid(int(dims), int(nx), int(ny) if int(dims) == 3 else 1, int(steps), float(dx),
+             float(dy), float(dz), int(split_order), int(zassenhaus))
+    best = Launch()
+    arr = (Launch * 8)()
+    n = _I(0)
+    st = L.bpm_tune(ctypes.byref(g), int(n_channels), int(steps), ctypes.byref(best), arr, 8,
+                    ctypes.byref(n))
+    if st != 0:
+        raise BpmError(st, L.bpm_last_error(None).decode())
+    return best.as_dict(), [arr[i].as_dict() for i in range(n.value)]
+
+
+def tune_save(path: str):
+    L = load()
+    if L.bpm_tune_save(os.fsencode(path)) != 0:
+        raise BpmError(1, L.bpm_last_error(None).decode())
+
+
+def tune_load(path: str) -> int:
+    L = load()
+    n = _I(0)
+    if L.bpm_tune_load(os.fsencode(path), ctypes.byref(n)) != 0:
+        raise BpmError(1, L.bpm_last_error(None).decode())
+    return n.value
+
+
+def tune_clear():
+    load().bpm_tune_clear()
 
 
 def plan_from_workload(w, stream=None, u=None) -> Plan:

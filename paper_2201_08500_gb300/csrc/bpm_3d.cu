@@ -145,15 +145,17 @@ struct Fft2Env {
   }
 };
 
-constexpr int kRowThreads = 256;
-
-// Row pass over R = 256 / T rows y0 .. y0 + R - 1 of one channel (T = NX/16).
+// Row pass over R = RT / T rows y0 .. y0 + R - 1 of one channel (T = NX/16,
+// RT = 256 or 512 threads: the tile height, and with it the length R x 8 bytes
+// of every column segment the transposed load / store moves, is a tuning
+// choice of the plan).
 // MODE 0: natural rows (e0, eh) in, forward x, transposed (s0, sh) out.
 // MODE 1: transposed in, inverse x, coupling, forward x, transposed out (in
 // place: every block reads and writes only its own rows of each column).
 // MODE 2: transposed in, inverse x, coupling, natural rows out.
-template <int NX, int MODE>
-__global__ void __launch_bounds__(kRowThreads, 2) row_pass_kernel(Pass3DArgs A) {
+template <int NX, int MODE, int RT>
+__global__ void __launch_bounds__(RT, 512 / RT) row_pass_kernel(Pass3DArgs A) {
+  constexpr int kRowThreads = RT;
   constexpr int T = NX / 16;
   constexpr int R = kRowThreads / T;  // rows per block
   constexpr int LD = R + 1;           // padded tile row (one column c)
@@ -212,10 +214,11 @@ __global__ void __launch_bounds__(kRowThreads, 2) row_pass_kernel(Pass3DArgs A) 
     const ChannelCoef cf = A.coef[ch];
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
+      // c = 0 marks vacuum, where the coupling is the identity (warp-uniform
+      // except at the crystal's surfaces: a warp holds consecutive x)
       const float2 c = __ldg(crow + t + T * k);
-      const bool in = (c.x != 0.f) || (c.y != 0.f);
-      const float ahx = in ? cf.a_hi.x : 1.f, ahy = in ? cf.a_hi.y : 0.f;
-      const float alx = in ? cf.a_lo.x : 0.f, aly = in ? cf.a_lo.y : 0.f;
+      if (c.x == 0.f && c.y == 0.f) continue;
+      const float ahx = cf.a_hi.x, ahy = cf.a_hi.y, alx = cf.a_lo.x, aly = cf.a_lo.y;
       const float2 bpc = c_mul(cf.bp, c);
       const float2 bmc = c_mulc(cf.bm, c);
       const float2 p = a[k], m = b[k];
@@ -346,9 +349,9 @@ __global__ void reduce3d_kernel(const float2* e0, const float2* eh, long long pl
   }
 }
 
-template <int NX, int MODE>
+template <int NX, int RT>
 size_t row_smem() {
-  return size_t(2) * NX * (kRowThreads / (NX / 16) + 1) * sizeof(float2);
+  return size_t(2) * NX * (RT / (NX / 16) + 1) * sizeof(float2);
 }
 
 template <int NY>
@@ -356,11 +359,11 @@ size_t col_smem() {
   return size_t(kColThreads / (NY / 16)) * 2 * NY * sizeof(float2);
 }
 
-template <int NX, int MODE>
+template <int NX, int MODE, int RT>
 cudaError_t row_launch(const Pass3DArgs& a, int n_ch, cudaStream_t s) {
-  constexpr int R = kRowThreads / (NX / 16);
+  constexpr int R = RT / (NX / 16);
   dim3 grid(unsigned((a.ny + R - 1) / R), unsigned(n_ch));
-  row_pass_kernel<NX, MODE><<<grid, kRowThreads, row_smem<NX, MODE>(), s>>>(a);
+  row_pass_kernel<NX, MODE, RT><<<grid, RT, row_smem<NX, RT>(), s>>>(a);
   return cudaGetLastError();
 }
 
@@ -372,15 +375,19 @@ cudaError_t col_launch(const Pass3DArgs& a, int n_ch, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int NX>
+template <int NX, int RT>
 cudaError_t row_attrs() {
   cudaError_t e = cudaSuccess, r;
-  if ((r = cudaFuncSetAttribute(row_pass_kernel<NX, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                int(row_smem<NX, 0>()))) != cudaSuccess) e = r;
-  if ((r = cudaFuncSetAttribute(row_pass_kernel<NX, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                int(row_smem<NX, 1>()))) != cudaSuccess) e = r;
-  if ((r = cudaFuncSetAttribute(row_pass_kernel<NX, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                int(row_smem<NX, 2>()))) != cudaSuccess) e = r;
+  const int smem = int(row_smem<NX, RT>());
+  if ((r = cudaFuncSetAttribute(row_pass_kernel<NX, 0, RT>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+    e = r;
+  if ((r = cudaFuncSetAttribute(row_pass_kernel<NX, 1, RT>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+    e = r;
+  if ((r = cudaFuncSetAttribute(row_pass_kernel<NX, 2, RT>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+    e = r;
   return e;
 }
 
@@ -399,23 +406,28 @@ bool pass3d_supported(int nx, int ny) {
 
 cudaError_t pass3d_set_attributes() {
   cudaError_t e = cudaSuccess, r;
-  if ((r = row_attrs<256>()) != cudaSuccess) e = r;
-  if ((r = row_attrs<512>()) != cudaSuccess) e = r;
-  if ((r = row_attrs<1024>()) != cudaSuccess) e = r;
+  if ((r = row_attrs<256, 256>()) != cudaSuccess) e = r;
+  if ((r = row_attrs<512, 256>()) != cudaSuccess) e = r;
+  if ((r = row_attrs<1024, 256>()) != cudaSuccess) e = r;
+  if ((r = row_attrs<256, 512>()) != cudaSuccess) e = r;
+  if ((r = row_attrs<512, 512>()) != cudaSuccess) e = r;
+  if ((r = row_attrs<1024, 512>()) != cudaSuccess) e = r;
   if ((r = col_attrs<256>()) != cudaSuccess) e = r;
   if ((r = col_attrs<512>()) != cudaSuccess) e = r;
   if ((r = col_attrs<1024>()) != cudaSuccess) e = r;
   return e;
 }
 
-cudaError_t launch_row_pass(int mode, const Pass3DArgs& a, int n_ch, cudaStream_t s) {
-#define BPM_ROW(NXV)                                          \
-  if (a.nx == NXV) {                                          \
-    if (mode == 0) return row_launch<NXV, 0>(a, n_ch, s);     \
-    if (mode == 1) return row_launch<NXV, 1>(a, n_ch, s);     \
-    return row_launch<NXV, 2>(a, n_ch, s);                    \
+cudaError_t launch_row_pass(int mode, int row_threads, const Pass3DArgs& a, int n_ch,
+                            cudaStream_t s) {
+#define BPM_ROW(NXV, RTV)                                                 \
+  if (a.nx == NXV && row_threads == RTV) {                                \
+    if (mode == 0) return row_launch<NXV, 0, RTV>(a, n_ch, s);            \
+    if (mode == 1) return row_launch<NXV, 1, RTV>(a, n_ch, s);            \
+    return row_launch<NXV, 2, RTV>(a, n_ch, s);                           \
   }
-  BPM_ROW(256) BPM_ROW(512) BPM_ROW(1024)
+  BPM_ROW(256, 256) BPM_ROW(512, 256) BPM_ROW(1024, 256)
+  BPM_ROW(256, 512) BPM_ROW(512, 512) BPM_ROW(1024, 512)
 #undef BPM_ROW
   return cudaErrorInvalidValue;
 }

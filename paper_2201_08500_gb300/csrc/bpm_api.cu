@@ -10,11 +10,13 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/bpm.h"
@@ -170,7 +172,8 @@ const DeviceInfo& device_info() {
     d.cc = prop.major * 10 + prop.minor;
     d.ok = true;
     if (d.cc == 103)
-      d.ok = march_set_attributes() == cudaSuccess && batch_set_attributes() == cudaSuccess &&
+      d.ok = march_set_attributes() == cudaSuccess && march_set_attributes_l2() == cudaSuccess &&
+             batch_set_attributes() == cudaSuccess &&
              setup_set_attributes() == cudaSuccess && pass3d_set_attributes() == cudaSuccess;
   }
   cache[dev] = d;
@@ -212,6 +215,7 @@ struct bpm_plan_s {
   float4* tables = nullptr;
   ChannelCoef* coef = nullptr;
   float2* twiddle = nullptr;
+  float2* twiddle_t = nullptr;   // 2D: stage twiddles in thread order
   int* rev = nullptr;
   double* gain = nullptr;
   double* omega = nullptr;
@@ -231,6 +235,8 @@ struct bpm_plan_s {
   size_t bytes = 0;               // device bytes owned by the plan
 
   int group = 1, blocks = 0;
+  int form = 0;  // march form: 0 tables in shared memory, 1 tables in L2 (two blocks / SM)
+  int row_threads = 256;  // 3D row pass tile: 256 or 512 threads
   bool timing = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bpm_stats stats{};
@@ -271,7 +277,7 @@ void free_plan_buffers(bpm_plan p) {
   void* ptrs[] = {p->cfield, p->e0,      p->eh,    p->tables, p->coef,     p->twiddle,
                   p->rev,    p->gain,    p->omega, p->weight, p->inc_norm, p->refl,
                   p->trans,  p->eh_time, p->dflag, p->u_tmp,  p->gcorr,    p->twy,
-                  p->qy,     p->spec,    p->twx3};
+                  p->qy,     p->spec,    p->twx3,  p->twiddle_t};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->ev0) cudaEventDestroy(p->ev0);
@@ -281,6 +287,38 @@ void free_plan_buffers(bpm_plan p) {
 bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 // Device bytes a 1D plan allocates (fields, tables, deformation factor, outputs).
+// Launch forms chosen by the autotuner, per shape, for this process.
+struct TuneEntry {
+  int form = 0, group = 1, row_threads = 256;
+  float ms = 0.f;
+};
+using TuneKey = std::tuple<int, int, int, int, int>;  // dims, nx, ny, split order, channels
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneEntry> g_tune;
+
+TuneKey tune_key(const bpm_grid& g, int n_ch) {
+  return TuneKey(g.dims, g.nx, g.dims == 3 ? g.ny : 1, g.split_order, n_ch);
+}
+
+// Whether a plan of grid g can run launch form (form, group, row_threads).
+bool launch_valid(const bpm_grid& g, int form, int group, int row_threads) {
+  if (g.dims == 3) return form == 0 && group == 1 && (row_threads == 256 || row_threads == 512);
+  const int maxg = march_max_group(g.nx);
+  if (row_threads != 256) return false;
+  if (form == 0) return group == 1 || group == maxg;
+  return form == 1 && g.split_order == 1 && march_l2_supported(g.nx, group);
+}
+
+// Derived launch quantities of the plan's form.
+void apply_launch(bpm_plan p) {
+  p->blocks = (p->n_ch + p->group - 1) / p->group;
+  p->stats.threads_per_channel = march_threads_per_channel(p->grid.nx);
+  p->stats.channels_per_block = p->group;
+  p->stats.blocks = p->blocks;
+  p->stats.smem_bytes = int(p->form == 1 ? march_l2_smem_bytes(p->grid.nx, p->group)
+                                         : march_smem_bytes(p->grid.nx, p->group));
+}
+
 size_t plan_bytes(const bpm_grid& g, int n_ch) {
   const size_t plane = size_t(g.nx) * (g.dims == 3 ? g.ny : 1);
   const size_t nf = size_t(n_ch) * plane;
@@ -293,6 +331,7 @@ size_t plan_bytes(const bpm_grid& g, int n_ch) {
          2 * nf * sizeof(float2);
   b += size_t(n_ch) * sizeof(ChannelCoef);
   b += size_t(g.nx) * (sizeof(float2) + sizeof(int) + sizeof(double));
+  if (g.dims == 2) b += size_t(g.nx) * sizeof(float2);  // thread-order twiddles
   b += size_t(n_ch) * (5 * sizeof(double) + sizeof(double2));
   b += nf * sizeof(double2);                       // time response
   return b;
@@ -375,6 +414,7 @@ BPM_API bpm_status bpm_plan_create(const bpm_grid* grid, int n_channels, void* c
   check(dalloc(&p->tables, size_t(n_channels) * 2 * g.nx), "alloc propagator tables");
   check(dalloc(&p->coef, size_t(n_channels)), "alloc coefficients");
   check(dalloc(&p->twiddle, size_t(g.nx)), "alloc twiddles");
+  if (g.dims == 2) check(dalloc(&p->twiddle_t, size_t(g.nx)), "alloc thread-order twiddles");
   check(dalloc(&p->rev, size_t(g.nx)), "alloc spectrum order");
   check(dalloc(&p->gain, size_t(g.nx)), "alloc gain");
   check(dalloc(&p->omega, size_t(n_channels)), "alloc omega");
@@ -396,14 +436,18 @@ BPM_API bpm_status bpm_plan_create(const bpm_grid* grid, int n_channels, void* c
     return st;
   }
   const FftConsts& fc = fft_consts(g.nx);
-  // Nx = 8192 reads its stage twiddles from memory in thread order (coalesced);
-  // smaller sizes load them into registers from the natural table.
-  const std::vector<float2> tw_ord = (g.dims == 2 && g.nx == 8192) ? twiddle_order(g.nx)
-                                                                   : std::vector<float2>();
-  check(cudaMemcpyAsync(p->twiddle, tw_ord.empty() ? fc.tw.data() : tw_ord.data(),
-                        sizeof(float2) * (tw_ord.empty() ? size_t(g.nx) : tw_ord.size()),
-                        cudaMemcpyHostToDevice, p->stream),
+  // The natural table feeds the kernels that keep twiddles in registers; the
+  // thread-ordered one those that read them from memory (Nx = 8192, L2 form).
+  check(cudaMemcpyAsync(p->twiddle, fc.tw.data(), sizeof(float2) * g.nx, cudaMemcpyHostToDevice,
+                        p->stream),
         "upload twiddles");
+  std::vector<float2> tw_ord;
+  if (g.dims == 2) {
+    tw_ord = twiddle_order(g.nx);
+    check(cudaMemcpyAsync(p->twiddle_t, tw_ord.data(), sizeof(float2) * tw_ord.size(),
+                          cudaMemcpyHostToDevice, p->stream),
+          "upload thread-order twiddles");
+  }
   check(cudaMemcpyAsync(p->rev, fc.rev.data(), sizeof(int) * g.nx, cudaMemcpyHostToDevice,
                         p->stream),
         "upload spectrum order");
@@ -442,11 +486,17 @@ BPM_API bpm_status bpm_plan_create(const bpm_grid* grid, int n_channels, void* c
   const int maxg = march_max_group(g.nx);
   const long long full = (n_channels + maxg - 1) / maxg;
   p->group = (maxg > 1 && full >= di.sm_count) ? maxg : 1;
-  p->blocks = (n_channels + p->group - 1) / p->group;
-  p->stats.threads_per_channel = march_threads_per_channel(g.nx);
-  p->stats.channels_per_block = p->group;
-  p->stats.blocks = p->blocks;
-  p->stats.smem_bytes = int(march_smem_bytes(g.nx, p->group));
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(tune_key(g, n_channels));
+    if (it != g_tune.end() &&
+        launch_valid(g, it->second.form, it->second.group, it->second.row_threads)) {
+      p->form = it->second.form;
+      p->group = it->second.group;
+      p->row_threads = it->second.row_threads;
+    }
+  }
+  apply_launch(p.get());
   p->bytes = plan_bytes(g, n_channels);
   *out = p.release();
   return BPM_OK;
@@ -587,6 +637,7 @@ BPM_API bpm_status bpm_run(bpm_plan p, int n_steps) {
   a.tables = p->tables;
   a.coef = p->coef;
   a.twiddle = p->twiddle;
+  a.twiddle_t = p->twiddle_t;
   a.cfield = p->cfield;
   a.e0 = p->e0;
   a.eh = p->eh;
@@ -600,7 +651,10 @@ BPM_API bpm_status bpm_run(bpm_plan p, int n_steps) {
   int launches = 0, march_launches = 0;
   if (p->timing) BPM_CUDA(p, cudaEventRecord(p->ev0, p->stream), "timing event");
   if (p->grid.dims == 2) {
-    BPM_CUDA(p, launch_march(p->grid.nx, p->group, p->blocks, a, p->stream), "march kernel");
+    if (p->form == 1 && !a.pre_couple)
+      BPM_CUDA(p, launch_march_l2(p->grid.nx, p->group, p->blocks, a, p->stream), "march kernel");
+    else
+      BPM_CUDA(p, launch_march(p->grid.nx, p->group, p->blocks, a, p->stream), "march kernel");
     march_launches = 1;
   } else if (n_steps > 0) {
     Pass3DArgs pa;
@@ -618,12 +672,12 @@ BPM_API bpm_status bpm_run(bpm_plan p, int n_steps) {
     pa.nx = p->grid.nx;
     pa.ny = p->grid.ny;
     pa.z = p->z;
-    BPM_CUDA(p, launch_row_pass(0, pa, p->n_ch, p->stream), "row pass");
+    BPM_CUDA(p, launch_row_pass(0, p->row_threads, pa, p->n_ch, p->stream), "row pass");
     march_launches = 1;
     for (int s = 0; s < n_steps; ++s) {
       pa.z = p->z + s;
       BPM_CUDA(p, launch_col_pass(pa, p->n_ch, p->stream), "column pass");
-      BPM_CUDA(p, launch_row_pass(s == n_steps - 1 ? 2 : 1, pa, p->n_ch, p->stream), "row pass");
+      BPM_CUDA(p, launch_row_pass(s == n_steps - 1 ? 2 : 1, p->row_threads, pa, p->n_ch, p->stream), "row pass");
       march_launches += 2;
     }
   }
@@ -736,6 +790,196 @@ BPM_API bpm_status bpm_get_stats(bpm_plan p, bpm_stats* out) {
   }
   *out = p->stats;
   return BPM_OK;
+}
+
+BPM_API bpm_status bpm_get_launch(bpm_plan p, bpm_launch* out) {
+  if (!p || !out) return fail(p, BPM_ERR_INVALID_ARG, "null argument");
+  out->form = p->form;
+  out->channels_per_block = p->group;
+  out->row_threads = p->row_threads;
+  out->ms = 0.f;
+  return BPM_OK;
+}
+
+BPM_API bpm_status bpm_set_launch(bpm_plan p, const bpm_launch* f) {
+  if (!p || !f) return fail(p, BPM_ERR_INVALID_ARG, "null argument");
+  if (!launch_valid(p->grid, f->form, f->channels_per_block, f->row_threads))
+    return fail(p, BPM_ERR_INVALID_ARG, "launch form not available for this plan");
+  p->form = f->form;
+  p->group = f->channels_per_block;
+  p->row_threads = f->row_threads;
+  apply_launch(p);
+  return BPM_OK;
+}
+
+namespace {
+
+std::string device_tag() {
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+    return "unknown";
+  std::string name(prop.name);
+  for (char& ch : name)
+    if (ch == ' ') ch = '_';
+  return name + "/" + std::to_string(prop.multiProcessorCount);
+}
+
+// Times `steps` steps of plan p in its current form: one warm-up, median of three.
+bpm_status time_form(bpm_plan p, int steps, cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+  float t[3];
+  for (int r = -1; r < 3; ++r) {
+    p->z = 0;
+    BPM_CUDA(p, cudaEventRecord(e0, p->stream), "tune event");
+    const bpm_status st = bpm_run(p, steps);
+    if (st != BPM_OK) return st;
+    BPM_CUDA(p, cudaEventRecord(e1, p->stream), "tune event");
+    BPM_CUDA(p, cudaEventSynchronize(e1), "tune sync");
+    if (r >= 0) BPM_CUDA(p, cudaEventElapsedTime(&t[r], e0, e1), "tune time");
+  }
+  std::sort(t, t + 3);
+  *ms = t[1];
+  return BPM_OK;
+}
+
+}  // namespace
+
+BPM_API bpm_status bpm_tune(const bpm_grid* grid, int n_channels, int steps, bpm_launch* best,
+                            bpm_launch* all, int max_all, int* n_all) {
+  if (!grid || !best || n_channels < 1 || steps < 1 || (all && max_all < 0))
+    return fail(nullptr, BPM_ERR_INVALID_ARG, "bpm_tune: bad arguments");
+  bpm_grid g = *grid;
+  g.nz = steps;
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(nullptr, BPM_ERR_CUDA, "bpm_tune: stream");
+  bpm_plan p = nullptr;
+  bpm_status st = bpm_plan_create(&g, n_channels, s, &p);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  std::vector<bpm_launch> meas;
+  if (st == BPM_OK) {
+    // synthetic content: a slab over the second quarter of x (vacuum elsewhere,
+    // as in Bragg geometry) and a Gaussian beam in front of it, channels around
+    // the Bragg condition of the 45-degree reflection at lambda = 1.26116 A
+    const double lam = 1.26116e-10, thb = 0.25 * kPiHost, width = g.nx * g.dx;
+    st = bpm_set_crystal(p, -1.0e-5, 1.0e-8, -4.0e-6, 5.0e-9, -4.0e-6, 5.0e-9, thb, lam,
+                         0.25 * width + 0.5 * g.dx, 0.25 * width, nullptr, 0);
+    std::vector<double> omega(n_channels), wgt(2 * size_t(n_channels), 0.0);
+    const double wb = 2.0 * kPiHost * 299792458.0 / lam;
+    for (int i = 0; i < n_channels; ++i) {
+      omega[i] = wb * (1.0 + 1.0e-5 + 8.0e-5 * (double(i) / n_channels - 0.5));
+      wgt[2 * size_t(i)] = 1.0;
+    }
+    const double w0 = width / 32.0;
+    if (st == BPM_OK)
+      st = bpm_set_pulse(p, omega.data(), wgt.data(), thb, width / 8.0, w0, 0.0,
+                         kPiHost * w0 * w0 / lam);
+    if (st == BPM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+      st = fail(nullptr, BPM_ERR_CUDA, "bpm_tune: events");
+    std::vector<bpm_launch> cand;
+    if (g.dims == 3) {
+      cand.push_back(bpm_launch{0, 1, 256, 0.f});
+      cand.push_back(bpm_launch{0, 1, 512, 0.f});
+    } else {
+      const int maxg = march_max_group(g.nx);
+      cand.push_back(bpm_launch{0, 1, 256, 0.f});
+      if (maxg > 1) cand.push_back(bpm_launch{0, maxg, 256, 0.f});
+      if (launch_valid(g, 1, maxg, 256)) cand.push_back(bpm_launch{1, maxg, 256, 0.f});
+    }
+    for (size_t i = 0; st == BPM_OK && i < cand.size(); ++i) {
+      st = bpm_set_launch(p, &cand[i]);
+      if (st == BPM_OK) st = time_form(p, steps, e0, e1, &cand[i].ms);
+      if (st == BPM_OK) meas.push_back(cand[i]);
+    }
+  }
+  const std::string err = st == BPM_OK ? std::string() : std::string(bpm_last_error(p));
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  bpm_plan_destroy(p);
+  cudaStreamDestroy(s);
+  if (st != BPM_OK) return fail(nullptr, st, "bpm_tune: " + err);
+  size_t b = 0;
+  for (size_t i = 1; i < meas.size(); ++i)
+    if (meas[i].ms < meas[b].ms) b = i;
+  *best = meas[b];
+  if (all)
+    for (int i = 0; i < int(meas.size()) && i < max_all; ++i) all[i] = meas[size_t(i)];
+  if (n_all) *n_all = int(meas.size());
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  TuneEntry te;
+  te.form = best->form;
+  te.group = best->channels_per_block;
+  te.row_threads = best->row_threads;
+  te.ms = best->ms;
+  g_tune[tune_key(*grid, n_channels)] = te;
+  return BPM_OK;
+}
+
+BPM_API bpm_status bpm_tune_save(const char* path) {
+  if (!path) return fail(nullptr, BPM_ERR_INVALID_ARG, "null path");
+  FILE* f = std::fopen(path, "w");
+  if (!f) return fail(nullptr, BPM_ERR_INVALID_ARG, std::string("cannot write ") + path);
+  const std::string tag = device_tag();
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  std::fprintf(f, "# libbpm launch forms: device dims nx ny split_order channels form "
+                  "channels_per_block row_threads ms\n");
+  for (const auto& kv : g_tune) {
+    const TuneKey& k = kv.first;
+    const TuneEntry& e = kv.second;
+    std::fprintf(f, "%s %d %d %d %d %d %d %d %d %.6f\n", tag.c_str(), std::get<0>(k),
+                 std::get<1>(k), std::get<2>(k), std::get<3>(k), std::get<4>(k), e.form, e.group,
+                 e.row_threads, double(e.ms));
+  }
+  const bool ok = std::fclose(f) == 0;
+  return ok ? BPM_OK : fail(nullptr, BPM_ERR_INVALID_ARG, std::string("cannot write ") + path);
+}
+
+BPM_API bpm_status bpm_tune_load(const char* path, int* n_loaded) {
+  if (!path) return fail(nullptr, BPM_ERR_INVALID_ARG, "null path");
+  FILE* f = std::fopen(path, "r");
+  if (!f) return fail(nullptr, BPM_ERR_INVALID_ARG, std::string("cannot read ") + path);
+  const std::string tag = device_tag();
+  std::map<TuneKey, TuneEntry> add;
+  char line[512];
+  bool bad = false;
+  while (std::fgets(line, sizeof line, f)) {
+    if (line[0] == '#' || line[0] == '\n') continue;
+    char dev[256];
+    int d, nx, ny, so, nch, form, grp, rt;
+    double ms;
+    if (std::sscanf(line, "%255s %d %d %d %d %d %d %d %d %lf", dev, &d, &nx, &ny, &so, &nch, &form,
+                    &grp, &rt, &ms) != 10) {
+      bad = true;
+      break;
+    }
+    if (tag != dev) continue;
+    bpm_grid g{};
+    g.dims = d;
+    g.nx = nx;
+    g.ny = ny;
+    g.split_order = so;
+    if (!launch_valid(g, form, grp, rt)) {
+      bad = true;
+      break;
+    }
+    TuneEntry e;
+    e.form = form;
+    e.group = grp;
+    e.row_threads = rt;
+    e.ms = float(ms);
+    add[TuneKey(d, nx, ny, so, nch)] = e;
+  }
+  std::fclose(f);
+  if (bad) return fail(nullptr, BPM_ERR_INVALID_ARG, std::string("malformed tune file ") + path);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (const auto& kv : add) g_tune[kv.first] = kv.second;
+  if (n_loaded) *n_loaded = int(add.size());
+  return BPM_OK;
+}
+
+BPM_API void bpm_tune_clear(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.clear();
 }
 
 BPM_API void bpm_plan_destroy(bpm_plan p) {
@@ -852,6 +1096,7 @@ MarchArgs march_args(bpm_plan p, int n_steps) {
   a.tables = p->tables;
   a.coef = p->coef;
   a.twiddle = p->twiddle;
+  a.twiddle_t = p->twiddle_t;
   a.cfield = p->cfield;
   a.e0 = p->e0;
   a.eh = p->eh;

@@ -24,6 +24,7 @@ struct MarchArgs {
   const float4* tables;      // [n_ch][2][16][T] {hi.re, hi.im, lo.re, lo.im}; env 0 = E0, 1 = Eh
   const ChannelCoef* coef;   // [n_ch]
   const float2* twiddle;     // [N] exp(-2 pi i k / N), FP32 correctly rounded
+  const float2* twiddle_t;   // stage twiddles in thread order (kernels that read them from memory)
   const float2* cfield;      // [nz][N] Pi(x, z) exp(+i h u(x, z)); 0 outside the crystal
   float2* e0;                // [n_ch][N]
   float2* eh;                // [n_ch][N]
@@ -97,13 +98,22 @@ int march_max_group(int n);
 size_t march_smem_bytes(int n, int group);
 cudaError_t launch_march(int n, int group, int blocks, const MarchArgs& a, cudaStream_t s);
 cudaError_t launch_march_strang(int n, int group, int blocks, const MarchArgs& a, cudaStream_t s);
+// Second form of the first-order march: propagator tables and stage twiddles
+// read from L2 instead of shared memory / registers, at most 128 registers, so
+// that two blocks (two channel groups at independent FFT phases) share an SM.
+bool march_l2_supported(int n, int group);
+size_t march_l2_smem_bytes(int n, int group);
+cudaError_t launch_march_l2(int n, int group, int blocks, const MarchArgs& a, cudaStream_t s);
+cudaError_t march_set_attributes_l2();
 cudaError_t march_set_attributes_strang();
 
 // 3D passes (bpm_3d.cu).  mode: 0 forward x only, 1 inverse x + coupling +
 // forward x, 2 inverse x + coupling.
 bool pass3d_supported(int nx, int ny);
 cudaError_t pass3d_set_attributes();
-cudaError_t launch_row_pass(int mode, const Pass3DArgs& a, int n_ch, cudaStream_t s);
+// row_threads: 256 or 512 (tile of 256/T or 512/T rows, T = nx/16)
+cudaError_t launch_row_pass(int mode, int row_threads, const Pass3DArgs& a, int n_ch,
+                            cudaStream_t s);
 cudaError_t launch_col_pass(const Pass3DArgs& a, int n_ch, cudaStream_t s);
 cudaError_t launch_reduce3d(const float2* e0, const float2* eh, long long plane, int n_ch,
                             const double* inc, double* refl, double* trans, cudaStream_t s);

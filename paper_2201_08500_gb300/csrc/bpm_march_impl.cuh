@@ -9,23 +9,24 @@
 namespace bpm {
 namespace {
 
-template <int N, int G, bool STRANG>
-__global__ void __launch_bounds__((N / 16) * G, 1) march_kernel(MarchArgs A) {
+template <int N, int G, bool STRANG, bool L2TAB = false>
+__global__ void __launch_bounds__((N / 16) * G, L2TAB ? 2 : 1) march_kernel(MarchArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
-  Resident<N, G, STRANG>::run(A, smem);
+  Resident<N, G, STRANG, L2TAB>::run(A, smem);
 }
 
-template <int N, int G, bool STRANG>
+template <int N, int G, bool STRANG, bool L2TAB = false>
 cudaError_t launch_one(int blocks, const MarchArgs& a, cudaStream_t s) {
-  march_kernel<N, G, STRANG><<<blocks, (N / 16) * G, Resident<N, G, STRANG>::smem_bytes(), s>>>(a);
+  march_kernel<N, G, STRANG, L2TAB>
+      <<<blocks, (N / 16) * G, Resident<N, G, STRANG, L2TAB>::smem_bytes(), s>>>(a);
   return cudaGetLastError();
 }
 
-template <int N, int G, bool STRANG>
+template <int N, int G, bool STRANG, bool L2TAB = false>
 cudaError_t attr_one() {
-  return cudaFuncSetAttribute(march_kernel<N, G, STRANG>,
+  return cudaFuncSetAttribute(march_kernel<N, G, STRANG, L2TAB>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(Resident<N, G, STRANG>::smem_bytes()));
+                              int(Resident<N, G, STRANG, L2TAB>::smem_bytes()));
 }
 
 }  // namespace

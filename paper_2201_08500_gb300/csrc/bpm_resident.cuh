@@ -23,14 +23,20 @@ BPM_DEV void group_sync(int g) {
   }
 }
 
-template <int N, int G, bool STRANG = false>
+// L2TAB selects the form with propagator tables and stage twiddles read from
+// L2 (thread-ordered, coalesced) and the deformation row loaded at the
+// coupling instead of prefetched, which fits in 128 registers and no table
+// shared memory: two blocks per SM then run their FFT exchanges and butterflies
+// at independent phases.
+template <int N, int G, bool STRANG = false, bool L2TAB = false>
 struct Resident {
   using Gm = Geom<N>;
   static constexpr int T = Gm::T;
   static constexpr int S = Gm::S;
   static constexpr int NTW = S - 1;                  // stages carrying inter-stage twiddles
-  static constexpr bool kTabSmem = (N <= 4096);      // propagator tables resident in smem
-  static constexpr bool kTwRegs = (N <= 4096);       // twiddles resident in registers
+  static constexpr bool kTabSmem = !L2TAB && (N <= 4096);  // propagator tables resident in smem
+  static constexpr bool kTwRegs = !L2TAB && (N <= 4096);   // twiddles resident in registers
+  static constexpr bool kPrefetchC = !L2TAB;               // deformation row loaded a step ahead
   static constexpr int kTwSlots = kTwRegs ? (NTW > 0 ? NTW : 1) : 1;
 
   __host__ __device__ static constexpr size_t tab_bytes() { return kTabSmem ? size_t(2) * N * sizeof(float4) : 0; }
@@ -219,14 +225,17 @@ struct Resident {
     }
     group_sync<T, G>(g);
 
+    const float2* tw = kTwRegs ? A.twiddle : A.twiddle_t;
     for (int step = 0; step < A.n_steps; ++step) {
       const float2* crow = A.cfield + size_t(A.z0 + step) * N;
       float2 c[16];
+      if constexpr (kPrefetchC || STRANG) {
 #pragma unroll
-      for (int k = 0; k < 16; ++k) c[k] = __ldg(crow + t + T * k);
+        for (int k = 0; k < 16; ++k) c[k] = __ldg(crow + t + T * k);
+      }
       if constexpr (STRANG) couple_row(a, b, c, cf);  // B(dz/2) A(dz) B(dz/2), half-step cf
 
-      fft_fwd(a, b, buf, twr, A.twiddle, t, g);
+      fft_fwd(a, b, buf, twr, tw, t, g);
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
         float4 pa, pb;
@@ -240,7 +249,11 @@ struct Resident {
         a[k] = c_mul2(a[k], pa);
         b[k] = c_mul2(b[k], pb);
       }
-      fft_inv(a, b, buf, twr, A.twiddle, t, g);
+      fft_inv(a, b, buf, twr, tw, t, g);
+      if constexpr (!kPrefetchC) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) c[k] = __ldg(crow + t + T * k);
+      }
       couple_row(a, b, c, cf);
     }
 

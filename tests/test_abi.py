@@ -42,3 +42,19 @@ def test_error_path_without_plan_is_reported():
     st = L.bpm_plan_create(bpm.ctypes.byref(grid), 0, None, bpm.ctypes.byref(h))
     assert st == 1  # INVALID_ARG: n_channels < 1 is rejected before any device call
     assert b"n_channels" in L.bpm_last_error(None)
+
+
+def test_tune_file_parsing_without_a_gpu(tmp_path):
+    """Tune files: comment lines are skipped, lines of another device are
+    ignored, malformed lines are an error (host logic only, no device call)."""
+    from paper_2201_08500_gb300 import bpm
+    bpm.load()
+    good = tmp_path / "tune.txt"
+    good.write_text("# header\nSomeOtherGPU/132 2 1024 1 1 611 0 4 256 1.5\n")
+    assert bpm.tune_load(str(good)) == 0
+    bad = tmp_path / "bad.txt"
+    bad.write_text("SomeOtherGPU/132 2 1024 one\n")
+    with pytest.raises(bpm.BpmError):
+        bpm.tune_load(str(bad))
+    with pytest.raises(bpm.BpmError):
+        bpm.tune_load(str(tmp_path / "missing.txt"))

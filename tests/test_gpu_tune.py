@@ -1,0 +1,94 @@
+"""Launch forms and their autotuner (bpm_tune): every form computes bitwise the
+same fields (only the layout of the work on the GPU differs), the tuner keeps
+the fastest measured form, and later plans of the shape use it."""
+import numpy as np
+import pytest
+
+import oracle.oracle as orc
+from paper_2201_08500_gb300 import bpm, workloads
+from test_gpu_parity import deformed_small, errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def device():
+    import torch
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+    bpm.tune_clear()
+    yield
+    bpm.tune_clear()
+
+
+def fields(w, **form):
+    p = bpm.plan_from_workload(w)
+    if form:
+        p.set_launch(**form)
+    got = p.launch()
+    p.run()
+    p.sync()
+    out = dict(e0=p.e0(), eh=p.eh(), R=p.reflectivity()[0])
+    p.close()
+    return out, got
+
+
+@pytest.mark.parametrize("nx,n_ch", [(1024, 611), (4096, 160)])
+def test_every_2d_form_gives_identical_fields(nx, n_ch):
+    w = deformed_small(nx, nz=48, n_ch=n_ch, seed=31)
+    maxg = {1024: 4, 4096: 1}[nx]
+    ref, _ = fields(w, form=0, channels_per_block=1)
+    forms = [dict(form=0, channels_per_block=maxg), dict(form=1, channels_per_block=maxg)]
+    for f in forms:
+        got, used = fields(w, **f)
+        assert used["form"] == f["form"] and used["channels_per_block"] == f["channels_per_block"]
+        for k in ("e0", "eh", "R"):
+            assert np.array_equal(got[k], ref[k]), (f, k)
+    e = errors(w, ref, channels=[0, n_ch // 2, n_ch - 1])
+    assert e["per_ch"] < 1e-4, e
+
+
+def test_3d_row_tiles_give_identical_fields():
+    from test_gpu_3d import case3d
+    w = case3d(512, 256, 16, 2, seed=5)
+    a, used_a = fields(w, row_threads=256)
+    b, used_b = fields(w, row_threads=512)
+    assert used_a["row_threads"] == 256 and used_b["row_threads"] == 512
+    assert np.array_equal(a["e0"], b["e0"]) and np.array_equal(a["eh"], b["eh"])
+
+
+def test_forms_a_plan_cannot_run_are_refused():
+    w = workloads.tiny(n_ch=4)
+    p = bpm.plan_from_workload(w)
+    with pytest.raises(bpm.BpmError):
+        p.set_launch(row_threads=384)
+    with pytest.raises(bpm.BpmError):
+        p.set_launch(channels_per_block=3)
+    p.close()
+    w.split_order = 2
+    q = bpm.plan_from_workload(w)
+    with pytest.raises(bpm.BpmError):
+        q.set_launch(form=1, channels_per_block=16)  # the L2 form is first order only
+    q.close()
+
+
+def test_tuner_keeps_the_fastest_and_later_plans_use_it(tmp_path):
+    bpm.tune_clear()
+    dx = 0.5e-6
+    best, every = bpm.tune(2, 1024, 1, dx, 0.0, dx, 611, steps=8)
+    assert len(every) == 3 and all(f["ms"] > 0 for f in every)
+    assert best["ms"] == min(f["ms"] for f in every)
+    want = {k: best[k] for k in ("form", "channels_per_block", "row_threads")}
+    p = bpm.Plan(2, 1024, 1, 30, dx, 0.0, dx, 611)
+    assert p.launch() == want
+    p.close()
+    path = str(tmp_path / "tune.txt")
+    bpm.tune_save(path)
+    bpm.tune_clear()
+    assert bpm.tune_load(path) == 1
+    q = bpm.Plan(2, 1024, 1, 30, dx, 0.0, dx, 611)
+    assert q.launch() == want
+    q.close()
+    b3, every3 = bpm.tune(3, 256, 256, 1e-6, 1e-6, 0.25e-6, 2, steps=4)
+    assert {f["row_threads"] for f in every3} == {256, 512}
+    bpm.tune_clear()

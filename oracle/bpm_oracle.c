@@ -16,8 +16,8 @@
  *     (Eqs. fov9, fov11, fov12) with the Zassenhaus-like factor on the
  *     zeroth term (the unnumbered equation after Eq. split-op);
  *   - the deformation phase exp(i n h u) (Eq. Authier);
- *   - the two-envelope split-step march (Eq. fov10, first-order splitting
- *     a1 = b1 = 1 of Eq. split-op);
+ *   - the two-envelope split-step march (Eq. fov10) with the first-, second-
+ *     or fourth-order operator splitting of Eq. split-op;
  *   - the incident Gaussian beam of the "Stationary problems" subsection.
  * Reflectivity and the frequency-to-time sum (Eq. ref:tdp and the text that
  * follows it) are plain sums and are written in oracle/oracle.py with numpy.
@@ -54,7 +54,7 @@ typedef struct {
   double dx, dy, dz;
   double chi0_re, chi0_im, chih_re, chih_im, chihb_re, chihb_im;
   double theta_B, lambda_B, x_surface, thickness;
-  int32_t zassenhaus, split_order; /* split_order 1: Eq. fov4; 2: Strang (a = (0,1), b = (1/2,1/2)) */
+  int32_t zassenhaus, split_order; /* Eq. split-op: 1 (Eq. fov4), 2 (Strang) or 4 (see orc_split_coefficients) */
   double theta_i, x0, w0, zx, zR;
   /* crystal shape (geometries by the crystal's boundaries, Section 2 end):
    * entrance surface x = x_surface + z tan_psi (asymmetric cut), slab
@@ -348,23 +348,72 @@ static void coupling_step(const orc_chan* c, const cplx* cf, const uint8_t* mk, 
   }
 }
 
+/* Coefficients (a_i, b_i) of the product in Eq. split-op, applied left to    */
+/* right, psi <- A(a_m dz) B(b_m dz) ... A(a_1 dz) B(b_1 dz) psi read as: for  */
+/* i = 1..m, propagate by a_i dz, then couple by b_i dz:                      */
+/*   order 1: a = (1), b = (1)                      (reduces to Eq. fov4)      */
+/*   order 2: a = (0, 1), b = (1/2, 1/2)            (Strang)                   */
+/*   order 4: a = (0, t, 1-2t, t), b = (t/2, (1-t)/2, (1-t)/2, t/2), with t    */
+/*            the root 1/(2 - 2^(1/3)) = 1.35120719... of 2t^3 + (1-2t)^3 = 0  */
+/*            (printed rounded as 1.3512).                                     */
+/* Returns m, or 0 for an unknown order.                                       */
+int orc_split_coefficients(int order, double* a, double* b) {
+  if (order == 0 || order == 1) {
+    a[0] = 1.0;
+    b[0] = 1.0;
+    return 1;
+  }
+  if (order == 2) {
+    a[0] = 0.0, a[1] = 1.0;
+    b[0] = 0.5, b[1] = 0.5;
+    return 2;
+  }
+  if (order == 4) {
+    double t = 1.0 / (2.0 - cbrt(2.0));
+    a[0] = 0.0, a[1] = t, a[2] = 1.0 - 2.0 * t, a[3] = t;
+    b[0] = 0.5 * t, b[1] = 0.5 * (1.0 - t), b[2] = 0.5 * (1.0 - t), b[3] = 0.5 * t;
+    return 4;
+  }
+  return 0;
+}
+
+/* Propagators of a fraction f of the step: exp(i f dz [sqrt(...) - k]).      */
+static void propagators_frac(const orc_problem* p, const orc_chan* c, double f, cplx* pp,
+                             cplx* pm) {
+  int ny = (p->dims == 3) ? p->ny : 1;
+  for (int r = 0; r < ny; ++r) {
+    double qy = (p->dims == 3) ? qfreq(r, p->ny, p->dy) : 0.0;
+    for (int m = 0; m < p->nx; ++m) {
+      double qx = qfreq(m, p->nx, p->dx);
+      pp[(size_t)r * p->nx + m] = propagator(c->k, qx + 0.5 * c->h, qy, f * p->dz);
+      pm[(size_t)r * p->nx + m] = propagator(c->k, qx - 0.5 * c->h, qy, f * p->dz);
+    }
+  }
+}
+
 /* Split-step z-march of Eq. fov10 for one channel, steps z_begin ..        */
 /* z_begin+n_steps-1, fields e0/eh ([ny][nx]) advanced in place.              */
-/* Step n: A+- <- IFFT(FFT(A+-) p+-), then in crystal cells                   */
-/*   A+ <- a A+ + bp c(x,z_n) A-,   A- <- a A- + bm conj(c(x,z_n)) A+          */
-/* using the values before the update.                                       */
+/* Step n is the product of Eq. split-op: for i = 1..m,                       */
+/*   A(a_i dz): A+- <- IFFT(FFT(A+-) p+-(a_i dz))       (skipped if a_i = 0)   */
+/*   B(b_i dz): in crystal cells, with the step coefficients of b_i dz,        */
+/*     A+ <- a A+ + bp c(x,z_n) A-,   A- <- a A- + bm conj(c(x,z_n)) A+        */
+/*     using the values before the update.                                    */
+/* Every B of step n takes Pi and u at z_n (the operator B of Eq. split-op is */
+/* written with delta-eps at the start of the step).                          */
 int orc_march(const orc_problem* p, const double* u, double omega, int z_begin, int n_steps,
               cplx* e0, cplx* eh) {
-  orc_chan c;
-  int strang = (p->split_order == 2);
-  /* Strang: B(dz/2) A(dz) B(dz/2), both half steps with Pi and u at z_n */
-  int rc = chan_setup_frac(p, omega, strang ? 0.5 : 1.0, &c);
-  if (rc) return rc;
-  if (p->split_order != 0 && p->split_order != 1 && p->split_order != 2) return 4;
+  double sa[4], sb[4];
+  int m = orc_split_coefficients(p->split_order, sa, sb);
+  if (m == 0) return 4;
+  orc_chan c[4];
+  for (int i = 0; i < m; ++i) {
+    int rc = chan_setup_frac(p, omega, sb[i], &c[i]);
+    if (rc) return rc;
+  }
   int ny = (p->dims == 3) ? p->ny : 1;
   size_t n = (size_t)p->nx * ny;
-  cplx* pp = (cplx*)malloc(sizeof(cplx) * n);
-  cplx* pm = (cplx*)malloc(sizeof(cplx) * n);
+  cplx* pp = (cplx*)malloc(sizeof(cplx) * n * (size_t)m);
+  cplx* pm = (cplx*)malloc(sizeof(cplx) * n * (size_t)m);
   cplx* cf = (cplx*)malloc(sizeof(cplx) * n);
   uint8_t* mk = (uint8_t*)malloc(n);
   if (!pp || !pm || !cf || !mk) {
@@ -374,7 +423,8 @@ int orc_march(const orc_problem* p, const double* u, double omega, int z_begin, 
     free(mk);
     return 2;
   }
-  orc_channel(p, omega, NULL, NULL, pp, pm);
+  for (int i = 0; i < m; ++i) propagators_frac(p, &c[i], sa[i], pp + n * i, pm + n * i);
+  int rc = 0;
   for (int s = 0; s < n_steps; ++s) {
     int zn = z_begin + s;
     if (zn < 0 || zn >= p->nz) {
@@ -382,16 +432,19 @@ int orc_march(const orc_problem* p, const double* u, double omega, int z_begin, 
       break;
     }
     orc_deformation(p, u, zn, cf, mk);
-    if (strang) coupling_step(&c, cf, mk, e0, eh, n);
-    orc_fft2(e0, p->nx, ny, -1);
-    orc_fft2(eh, p->nx, ny, -1);
-    for (size_t i = 0; i < n; ++i) {
-      e0[i] *= pp[i];
-      eh[i] *= pm[i];
+    for (int i = 0; i < m; ++i) {
+      if (sa[i] != 0.0) {
+        orc_fft2(e0, p->nx, ny, -1);
+        orc_fft2(eh, p->nx, ny, -1);
+        for (size_t j = 0; j < n; ++j) {
+          e0[j] *= pp[n * i + j];
+          eh[j] *= pm[n * i + j];
+        }
+        orc_fft2(e0, p->nx, ny, +1);
+        orc_fft2(eh, p->nx, ny, +1);
+      }
+      coupling_step(&c[i], cf, mk, e0, eh, n);
     }
-    orc_fft2(e0, p->nx, ny, +1);
-    orc_fft2(eh, p->nx, ny, +1);
-    coupling_step(&c, cf, mk, e0, eh, n);
   }
   free(pp);
   free(pm);

@@ -516,3 +516,57 @@ def test_laue_slab_pendelloesung():
         t = (nb - na) * dz
         ratio = np.mean(np.abs(eh[0]) ** 2) / np.mean(np.abs(init[0]) ** 2)
         assert abs(ratio - math.sin(math.pi * t / L0) ** 2) < 1e-3
+
+
+def _slab_screen_run(order, nz, chih=0j, Z=20e-6):
+    """A chi0 slab whose two edges lie inside a Gaussian beam (diffraction and
+    the susceptibility step do not commute at the edges)."""
+    w = make(nx=256, nz=nz, dz=Z / nz, x_surface=100.5 * 0.5e-6, thickness=60 * 0.5e-6,
+             x0=128 * 0.5e-6, w0=20 * 0.5e-6, chi0=complex(-1e-5, 2e-7), chih=chih, chihb=chih,
+             split_order=order)
+    e0, eh, init = orc.run(w, n_threads=1)
+    return np.concatenate([e0[0], eh[0]]), np.linalg.norm(init)
+
+
+def test_fourth_order_splitting_converges_at_fourth_order():
+    """Eq. split-op with t = 1/(2 - 2^(1/3)), a = (0, t, 1-2t, t),
+    b = (t/2, (1-t)/2, (1-t)/2, t/2): with chi_h = 0 the coupling operator B is
+    an exact phase screen, so the splitting error alone remains and halving dz
+    divides it by 2^4 (first order: 2, Strang: 4), all to the same limit."""
+    ref, n0 = _slab_screen_run(4, 1280)
+    ref2, _ = _slab_screen_run(2, 1280)
+    assert np.linalg.norm(ref - ref2) / n0 < 1e-5
+    ratio = {}
+    for order in (1, 2, 4):
+        e = [np.linalg.norm(_slab_screen_run(order, n)[0] - ref) / n0 for n in (40, 80, 160)]
+        ratio[order] = (e[0] / e[1], e[1] / e[2])
+    assert all(1.8 < r < 2.3 for r in ratio[1]), ratio
+    assert all(3.6 < r < 4.6 for r in ratio[2]), ratio
+    assert all(12.0 < r < 20.0 for r in ratio[4]), ratio
+
+
+def test_fourth_order_with_coupling_is_limited_by_the_truncated_expansion():
+    """With chi_h != 0 the three-term Jacobi-Anger coupling differs from the
+    exact two-beam rotation by O(w^3) per step (i J1(w) vs i sin(w/2)), so
+    every splitting converges at most as dz^2, and orders 2 and 4 share the
+    limit."""
+    chih = complex(-4e-6, 0.0)
+    ref, n0 = _slab_screen_run(4, 1280, chih)
+    ref2, _ = _slab_screen_run(2, 1280, chih)
+    assert np.linalg.norm(ref - ref2) / n0 < 1e-5
+    e = [np.linalg.norm(_slab_screen_run(4, n, chih)[0] - ref) / n0 for n in (40, 80, 160)]
+    assert 3.5 < e[0] / e[1] < 4.7 and 3.5 < e[1] / e[2] < 4.7
+
+
+def test_split_orders_agree_in_free_space():
+    """With chi = 0 every B is the identity and the propagation fractions of
+    each order add up to one step: A(t) A(1-2t) A(t) = A(dz) exactly, so all
+    orders give the same fields up to rounding (FP64 rounding of the tilted
+    propagator's phase, about -6e3 rad per step here, allows 1e-10)."""
+    base = dict(nx=256, nz=12, chi0=0j, chih=0j, chihb=0j, x0=100 * 0.5e-6, w0=8 * 0.5e-6)
+    f1 = orc.run(make(split_order=1, **base), n_threads=1)
+    for order in (2, 4):
+        fo = orc.run(make(split_order=order, **base), n_threads=1)
+        n0 = np.linalg.norm(f1[2])
+        assert np.linalg.norm(fo[0] - f1[0]) / n0 < 1e-10
+        assert np.linalg.norm(fo[1]) == 0.0

@@ -60,7 +60,10 @@ typedef struct bpm_plan_s* bpm_plan;
  * nx (and ny) are powers of two: 256..8192 for dims = 2, 64..1024 for dims = 3.
  * split_order (Eq. split-op): 1 = first order (a1 = b1 = 1, Eq. fov4); 2 = Strang
  * (a = (0, 1), b = (1/2, 1/2): half coupling, propagation, half coupling, both
- * halves with Pi and u sampled at z_n; dims = 2 only).  zassenhaus: 1 applies exp(D2 dz-hat^2/2),
+ * halves with Pi and u sampled at z_n; dims = 2 only); 4 = fourth order
+ * (t = 1/(2 - 2^(1/3)), a = (0, t, 1-2t, t), b = (t/2, (1-t)/2, (1-t)/2, t/2),
+ * every coupling at z_n; dims = 2 only, single plans (not batches), and every
+ * transverse mode must propagate: pi/dx + h/2 < k).  zassenhaus: 1 applies exp(D2 dz-hat^2/2),
  * D2 = (chi_h/2/cos alpha)^2, to the zeroth Jacobi-Anger term (Section 2,
  * equation after Eq. split-op); 0 leaves it out. */
 typedef struct {
@@ -75,7 +78,8 @@ typedef struct {
  * cudaStream_t; NULL = legacy default stream).  Validates the grid and
  * allocates the plan's device buffers.
  * Errors: INVALID_ARG (null pointers, n_channels < 1, non-positive steps),
- * UNSUPPORTED (sizes outside the list above, split_order != 1), OOM, CUDA. */
+ * UNSUPPORTED (sizes outside the list above, split_order not 1, 2 or 4, or
+ * not 1 in 3D), OOM, CUDA. */
 BPM_API bpm_status bpm_plan_create(const bpm_grid* grid, int n_channels, void* cuda_stream,
                                    bpm_plan* out);
 
@@ -112,7 +116,8 @@ BPM_API bpm_status bpm_set_geometry(bpm_plan plan, double tan_psi, double z_begi
  * builds the propagator tables, the coupling coefficients and the incident
  * field A+ = S_i g(x, y) exp(i (k_i sin theta_i - h/2) x), A- = 0, and resets
  * the march to z = 0.  Requires bpm_set_crystal first.
- * Errors: INVALID_ARG (null arrays, k_i <= h/2), STATE, OOM, CUDA. */
+ * Errors: INVALID_ARG (null arrays, k_i <= h/2), UNSUPPORTED (split_order 4 with
+ * a non-propagating mode), STATE, OOM, CUDA. */
 BPM_API bpm_status bpm_set_pulse(bpm_plan plan, const double* omega, const double* weight_re_im,
                                  double theta_i, double x0, double w0, double zx, double zR);
 

@@ -325,11 +325,12 @@ size_t plan_bytes(const bpm_grid& g, int n_ch) {
   size_t b = 0;
   b += size_t(g.nz) * plane * sizeof(float2);      // deformation factor
   b += 2 * nf * sizeof(float2);                    // E0, Eh
-  b += size_t(n_ch) * 2 * g.nx * sizeof(float4);   // propagator tables (3D: column anchors)
+  const size_t sets = g.split_order == 4 ? 2 : 1;   // table / coefficient sets per channel
+  b += sets * n_ch * 2 * g.nx * sizeof(float4);     // propagator tables (3D: column anchors)
   if (g.dims == 3)
     b += size_t(n_ch) * 2 * g.nx * sizeof(float) + size_t(g.ny) * 2 * sizeof(float2) +
          2 * nf * sizeof(float2);
-  b += size_t(n_ch) * sizeof(ChannelCoef);
+  b += sets * n_ch * sizeof(ChannelCoef);
   b += size_t(g.nx) * (sizeof(float2) + sizeof(int) + sizeof(double));
   if (g.dims == 2) b += size_t(g.nx) * sizeof(float2);  // thread-order twiddles
   b += size_t(n_ch) * (5 * sizeof(double) + sizeof(double2));
@@ -372,9 +373,9 @@ BPM_API bpm_status bpm_plan_create(const bpm_grid* grid, int n_channels, void* c
   if (n_channels < 1) return fail(nullptr, BPM_ERR_INVALID_ARG, "n_channels must be >= 1");
   if (g.nz < 1 || !(g.dx > 0) || !(g.dz > 0))
     return fail(nullptr, BPM_ERR_INVALID_ARG, "nz, dx and dz must be positive");
-  if (g.split_order != 1 && g.split_order != 2)
-    return fail(nullptr, BPM_ERR_UNSUPPORTED, "split_order must be 1 or 2");
-  if (g.split_order == 2 && g.dims != 2)
+  if (g.split_order != 1 && g.split_order != 2 && g.split_order != 4)
+    return fail(nullptr, BPM_ERR_UNSUPPORTED, "split_order must be 1, 2 or 4");
+  if (g.split_order != 1 && g.dims != 2)
     return fail(nullptr, BPM_ERR_UNSUPPORTED, "Strang splitting is implemented for 2D plans");
   if (g.dims == 2) {
     if (g.ny != 1) return fail(nullptr, BPM_ERR_INVALID_ARG, "dims = 2 requires ny = 1");
@@ -411,8 +412,9 @@ BPM_API bpm_status bpm_plan_create(const bpm_grid* grid, int n_channels, void* c
   check(dalloc(&p->cfield, size_t(g.nz) * p->plane), "alloc deformation field");
   check(dalloc(&p->e0, nf), "alloc E0");
   check(dalloc(&p->eh, nf), "alloc Eh");
-  check(dalloc(&p->tables, size_t(n_channels) * 2 * g.nx), "alloc propagator tables");
-  check(dalloc(&p->coef, size_t(n_channels)), "alloc coefficients");
+  const size_t sets = g.split_order == 4 ? 2 : 1;  // Eq. split-op order 4: two of each
+  check(dalloc(&p->tables, sets * n_channels * 2 * g.nx), "alloc propagator tables");
+  check(dalloc(&p->coef, sets * n_channels), "alloc coefficients");
   check(dalloc(&p->twiddle, size_t(g.nx)), "alloc twiddles");
   if (g.dims == 2) check(dalloc(&p->twiddle_t, size_t(g.nx)), "alloc thread-order twiddles");
   check(dalloc(&p->rev, size_t(g.nx)), "alloc spectrum order");
@@ -529,6 +531,7 @@ BPM_API bpm_status bpm_set_crystal(bpm_plan p, double chi0_re, double chi0_im, d
   sa.chihb_im = chihbar_im;
   sa.zassenhaus = p->grid.zassenhaus ? 1 : 0;
   sa.coupling_frac = p->grid.split_order == 2 ? 0.5 : 1.0;
+  sa.split_order = p->grid.split_order;
   sa.x_surface = x_surface;
   sa.x_end = x_surface + thickness;
   if (!p->have_geometry) {
@@ -583,6 +586,15 @@ BPM_API bpm_status bpm_set_pulse(bpm_plan p, const double* omega, const double* 
   for (int i = 0; i < p->n_ch; ++i)
     if (!(omega[i] / 299792458.0 > 0.5 * p->sa.h))
       return fail(p, BPM_ERR_INVALID_ARG, "a channel has k <= h/2 (no Bragg solution)");
+  if (p->grid.split_order == 4) {
+    // the propagation 1-2t < 0 runs backwards: an evanescent mode would grow by
+    // exp((2t-1) dz kappa) before the forward steps damp it; require every
+    // mode of the grid to propagate, |q| + h/2 < k
+    const double qmax = kPiHost / p->grid.dx + 0.5 * p->sa.h;
+    for (int i = 0; i < p->n_ch; ++i)
+      if (!(omega[i] / 299792458.0 > qmax))
+        return fail(p, BPM_ERR_UNSUPPORTED, "fourth-order splitting needs propagating modes only");
+  }
   if (p->grid.dims == 3) {
     // the column pass expands sqrt(K^2 - qy^2) - K to second order in
     // c = dz qy^2 / (2K): require every K^2 > 0 and c < 1e-3 (terms dropped < 2e-10)
@@ -647,11 +659,11 @@ BPM_API bpm_status bpm_run(bpm_plan p, int n_steps) {
   a.n_ch = p->n_ch;
   a.z0 = p->z;
   a.n_steps = n_steps;
-  a.pre_couple = p->grid.split_order == 2 ? 1 : 0;
+  a.split_order = p->grid.split_order;
   int launches = 0, march_launches = 0;
   if (p->timing) BPM_CUDA(p, cudaEventRecord(p->ev0, p->stream), "timing event");
   if (p->grid.dims == 2) {
-    if (p->form == 1 && !a.pre_couple)
+    if (p->form == 1 && a.split_order == 1)
       BPM_CUDA(p, launch_march_l2(p->grid.nx, p->group, p->blocks, a, p->stream), "march kernel");
     else
       BPM_CUDA(p, launch_march(p->grid.nx, p->group, p->blocks, a, p->stream), "march kernel");
@@ -1106,7 +1118,7 @@ MarchArgs march_args(bpm_plan p, int n_steps) {
   a.n_ch = p->n_ch;
   a.z0 = p->z;
   a.n_steps = n_steps;
-  a.pre_couple = p->grid.split_order == 2 ? 1 : 0;
+  a.split_order = p->grid.split_order;
   return a;
 }
 
@@ -1223,6 +1235,8 @@ BPM_API bpm_status bpm_batch_submit(bpm_batch b, bpm_plan p, uint64_t* ticket) {
   if (!b || !p || !ticket) return bfail(b, BPM_ERR_INVALID_ARG, "null argument");
   if (!p->have_pulse) return bfail(b, BPM_ERR_STATE, "plan needs crystal and pulse first");
   if (p->grid.dims != 2) return bfail(b, BPM_ERR_UNSUPPORTED, "batches take 2D plans");
+  if (p->grid.split_order == 4)
+    return bfail(b, BPM_ERR_UNSUPPORTED, "batches take split orders 1 and 2");
   for (const auto& e : b->entries)
     if (e.plan == p) return bfail(b, BPM_ERR_STATE, "plan already in the batch");
   if (b->budget && b->used + p->bytes > b->budget)

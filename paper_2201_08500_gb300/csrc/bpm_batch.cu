@@ -45,11 +45,11 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
     const BatchItem item = items[it];
     const MarchArgs& A = plans[item.plan];
     switch (item.n) {
-      case 256: Resident<256, 16, STRANG>::run_item(A, item.ch0, smem); break;
-      case 512: Resident<512, 8, STRANG>::run_item(A, item.ch0, smem); break;
-      case 1024: Resident<1024, 4, STRANG>::run_item(A, item.ch0, smem); break;
-      case 2048: Resident<2048, 2, STRANG>::run_item(A, item.ch0, smem); break;
-      case 4096: Resident<4096, 1, STRANG>::run_item(A, item.ch0, smem); break;
+      case 256: Resident<256, 16, STRANG ? 2 : 1>::run_item(A, item.ch0, smem); break;
+      case 512: Resident<512, 8, STRANG ? 2 : 1>::run_item(A, item.ch0, smem); break;
+      case 1024: Resident<1024, 4, STRANG ? 2 : 1>::run_item(A, item.ch0, smem); break;
+      case 2048: Resident<2048, 2, STRANG ? 2 : 1>::run_item(A, item.ch0, smem); break;
+      case 4096: Resident<4096, 1, STRANG ? 2 : 1>::run_item(A, item.ch0, smem); break;
       default: break;
     }
   }
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(512, 1)
     const int it = s_item;
     if (it >= n_items) break;
     const BatchItem item = items[it];
-    if (item.n == 8192) Resident<8192, 1, STRANG>::run_item(plans[item.plan], item.ch0, smem);
+    if (item.n == 8192) Resident<8192, 1, STRANG ? 2 : 1>::run_item(plans[item.plan], item.ch0, smem);
   }
 }
 

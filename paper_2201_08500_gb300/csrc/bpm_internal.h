@@ -34,7 +34,7 @@ struct MarchArgs {
   int n_ch;
   int z0;
   int n_steps;
-  int pre_couple;            // 1: Strang splitting, a half coupling before each propagation
+  int split_order;           // Eq. split-op: 1, 2 (Strang) or 4 (tables and coef then hold two sets)
 };
 
 // Arguments of the 3D row / column passes (bpm_3d.cu).
@@ -60,7 +60,8 @@ struct SetupArgs {
   double h;                  // reciprocal-lattice vector
   double chi0_re, chi0_im, chih_re, chih_im, chihb_re, chihb_im;
   int zassenhaus;
-  double coupling_frac;      // fraction of dz per coupling application (Strang: 1/2)
+  double coupling_frac;      // fraction of dz per coupling application (3D: 1)
+  int split_order;           // 2D tables: Eq. split-op order 1, 2 or 4
   double x_surface, x_end;   // slab [x_surface, x_end) at z = 0
   double tan_psi;            // entrance surface x = x_surface + z tan_psi (asymmetric cut)
   double z_begin, z_end;     // crystal only for z_begin <= z < z_end (Laue slab)
@@ -106,6 +107,10 @@ size_t march_l2_smem_bytes(int n, int group);
 cudaError_t launch_march_l2(int n, int group, int blocks, const MarchArgs& a, cudaStream_t s);
 cudaError_t march_set_attributes_l2();
 cudaError_t march_set_attributes_strang();
+// Fourth-order splitting (Eq. split-op, a = (0, t, 1-2t, t), b = (t/2, (1-t)/2, (1-t)/2, t/2)).
+cudaError_t launch_march_split4(int n, int group, int blocks, const MarchArgs& a, cudaStream_t s);
+cudaError_t march_set_attributes_split4();
+size_t march_split4_smem_bytes(int n, int group);
 
 // 3D passes (bpm_3d.cu).  mode: 0 forward x only, 1 inverse x + coupling +
 // forward x, 2 inverse x + coupling.

@@ -51,20 +51,22 @@ size_t march_smem_bytes(int n, int group) {
 
 cudaError_t march_set_attributes() {
   cudaError_t e = march_set_attributes_strang();
-  cudaError_t r[] = {attr_one<256, 1, false>(),  attr_one<256, 16, false>(),
-                     attr_one<512, 1, false>(),  attr_one<512, 8, false>(),
-                     attr_one<1024, 1, false>(), attr_one<1024, 4, false>(),
-                     attr_one<2048, 1, false>(), attr_one<2048, 2, false>(),
-                     attr_one<4096, 1, false>(), attr_one<8192, 1, false>()};
+  if (cudaError_t e4 = march_set_attributes_split4(); e4 != cudaSuccess) e = e4;
+  cudaError_t r[] = {attr_one<256, 1, 1>(),  attr_one<256, 16, 1>(),
+                     attr_one<512, 1, 1>(),  attr_one<512, 8, 1>(),
+                     attr_one<1024, 1, 1>(), attr_one<1024, 4, 1>(),
+                     attr_one<2048, 1, 1>(), attr_one<2048, 2, 1>(),
+                     attr_one<4096, 1, 1>(), attr_one<8192, 1, 1>()};
   for (cudaError_t x : r)
     if (x != cudaSuccess) e = x;
   return e;
 }
 
 cudaError_t launch_march(int n, int group, int blocks, const MarchArgs& a, cudaStream_t s) {
-  if (a.pre_couple) return launch_march_strang(n, group, blocks, a, s);
+  if (a.split_order == 2) return launch_march_strang(n, group, blocks, a, s);
+  if (a.split_order == 4) return launch_march_split4(n, group, blocks, a, s);
 #define BPM_LAUNCH_CASE(NN, GG) \
-  if (n == NN && group == GG) return launch_one<NN, GG, false>(blocks, a, s);
+  if (n == NN && group == GG) return launch_one<NN, GG, 1>(blocks, a, s);
   BPM_LAUNCH_CASE(256, 1) BPM_LAUNCH_CASE(256, 16)
   BPM_LAUNCH_CASE(512, 1) BPM_LAUNCH_CASE(512, 8)
   BPM_LAUNCH_CASE(1024, 1) BPM_LAUNCH_CASE(1024, 4)

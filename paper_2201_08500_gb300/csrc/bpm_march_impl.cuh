@@ -1,5 +1,6 @@
 // Single-plan launch wrappers of the resident march kernel, shared by the
-// first-order (bpm_march.cu) and Strang (bpm_march_strang.cu) translation units.
+// translation units of each splitting order (bpm_march.cu: first order,
+// bpm_march_strang.cu: second, bpm_march_split4.cu: fourth) and form.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -9,24 +10,24 @@
 namespace bpm {
 namespace {
 
-template <int N, int G, bool STRANG, bool L2TAB = false>
+template <int N, int G, int SPLIT, bool L2TAB = false>
 __global__ void __launch_bounds__((N / 16) * G, L2TAB ? 2 : 1) march_kernel(MarchArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
-  Resident<N, G, STRANG, L2TAB>::run(A, smem);
+  Resident<N, G, SPLIT, L2TAB>::run(A, smem);
 }
 
-template <int N, int G, bool STRANG, bool L2TAB = false>
+template <int N, int G, int SPLIT, bool L2TAB = false>
 cudaError_t launch_one(int blocks, const MarchArgs& a, cudaStream_t s) {
-  march_kernel<N, G, STRANG, L2TAB>
-      <<<blocks, (N / 16) * G, Resident<N, G, STRANG, L2TAB>::smem_bytes(), s>>>(a);
+  march_kernel<N, G, SPLIT, L2TAB>
+      <<<blocks, (N / 16) * G, Resident<N, G, SPLIT, L2TAB>::smem_bytes(), s>>>(a);
   return cudaGetLastError();
 }
 
-template <int N, int G, bool STRANG, bool L2TAB = false>
+template <int N, int G, int SPLIT, bool L2TAB = false>
 cudaError_t attr_one() {
-  return cudaFuncSetAttribute(march_kernel<N, G, STRANG, L2TAB>,
+  return cudaFuncSetAttribute(march_kernel<N, G, SPLIT, L2TAB>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(Resident<N, G, STRANG, L2TAB>::smem_bytes()));
+                              int(Resident<N, G, SPLIT, L2TAB>::smem_bytes()));
 }
 
 }  // namespace

@@ -8,11 +8,11 @@ namespace bpm {
 
 cudaError_t march_set_attributes_strang() {
   cudaError_t e = cudaSuccess;
-  cudaError_t r[] = {attr_one<256, 1, true>(),  attr_one<256, 16, true>(),
-                     attr_one<512, 1, true>(),  attr_one<512, 8, true>(),
-                     attr_one<1024, 1, true>(), attr_one<1024, 4, true>(),
-                     attr_one<2048, 1, true>(), attr_one<2048, 2, true>(),
-                     attr_one<4096, 1, true>(), attr_one<8192, 1, true>()};
+  cudaError_t r[] = {attr_one<256, 1, 2>(),  attr_one<256, 16, 2>(),
+                     attr_one<512, 1, 2>(),  attr_one<512, 8, 2>(),
+                     attr_one<1024, 1, 2>(), attr_one<1024, 4, 2>(),
+                     attr_one<2048, 1, 2>(), attr_one<2048, 2, 2>(),
+                     attr_one<4096, 1, 2>(), attr_one<8192, 1, 2>()};
   for (cudaError_t x : r)
     if (x != cudaSuccess) e = x;
   return e;
@@ -20,7 +20,7 @@ cudaError_t march_set_attributes_strang() {
 
 cudaError_t launch_march_strang(int n, int group, int blocks, const MarchArgs& a, cudaStream_t s) {
 #define BPM_STRANG_CASE(NN, GG) \
-  if (n == NN && group == GG) return launch_one<NN, GG, true>(blocks, a, s);
+  if (n == NN && group == GG) return launch_one<NN, GG, 2>(blocks, a, s);
   BPM_STRANG_CASE(256, 1) BPM_STRANG_CASE(256, 16)
   BPM_STRANG_CASE(512, 1) BPM_STRANG_CASE(512, 8)
   BPM_STRANG_CASE(1024, 1) BPM_STRANG_CASE(1024, 4)

@@ -28,13 +28,22 @@ BPM_DEV void group_sync(int g) {
 // coupling instead of prefetched, which fits in 128 registers and no table
 // shared memory: two blocks per SM then run their FFT exchanges and butterflies
 // at independent phases.
-template <int N, int G, bool STRANG = false, bool L2TAB = false>
+//
+// SPLIT is the order of the operator splitting of Eq. split-op: 1 (propagate,
+// couple), 2 (Strang: half couple, propagate, half couple) or 4 (couple t/2,
+// propagate t, couple (1-t)/2, propagate 1-2t, couple (1-t)/2, propagate t,
+// couple t/2; two propagator tables and two coefficient sets per channel,
+// tables read from L2).  Every coupling of step n uses c(x, z_n).
+template <int N, int G, int SPLIT = 1, bool L2TAB = false>
 struct Resident {
+  static_assert(SPLIT == 1 || SPLIT == 2 || SPLIT == 4, "splitting order");
+  static constexpr bool STRANG = (SPLIT == 2);
+  static constexpr int kTabs = SPLIT == 4 ? 2 : 1;   // propagator tables per channel
   using Gm = Geom<N>;
   static constexpr int T = Gm::T;
   static constexpr int S = Gm::S;
   static constexpr int NTW = S - 1;                  // stages carrying inter-stage twiddles
-  static constexpr bool kTabSmem = !L2TAB && (N <= 4096);  // propagator tables resident in smem
+  static constexpr bool kTabSmem = !L2TAB && SPLIT != 4 && (N <= 4096);  // tables resident in smem
   static constexpr bool kTwRegs = !L2TAB && (N <= 4096);   // twiddles resident in registers
   static constexpr bool kPrefetchC = !L2TAB;               // deformation row loaded a step ahead
   static constexpr int kTwSlots = kTwRegs ? (NTW > 0 ? NTW : 1) : 1;
@@ -200,6 +209,28 @@ struct Resident {
     }
   }
 
+  // One propagation A of Eq. split-op: forward FFT, the digit-reversed spectra
+  // times the tilted propagators (smem copy `tab` or table `gt` in L2), inverse FFT.
+  static BPM_DEV void propagate(float2 (&a)[16], float2 (&b)[16], float2* buf, const float4* tab,
+                                const float4* gt, const float2 (&twr)[kTwSlots][15],
+                                const float2* tw, int t, int g) {
+    fft_fwd(a, b, buf, twr, tw, t, g);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      float4 pa, pb;
+      if constexpr (kTabSmem) {
+        pa = tab[k * T + t];
+        pb = tab[N + k * T + t];
+      } else {
+        pa = __ldg(gt + k * T + t);
+        pb = __ldg(gt + N + k * T + t);
+      }
+      a[k] = c_mul2(a[k], pa);
+      b[k] = c_mul2(b[k], pb);
+    }
+    fft_inv(a, b, buf, twr, tw, t, g);
+  }
+
   // March channel ch of plan A by A.n_steps steps from z = A.z0 (this thread's
   // channel group g; T threads).  Ends with the group barrier, so the group's
   // shared memory may be reused afterwards.
@@ -210,11 +241,11 @@ struct Resident {
     float2* buf = reinterpret_cast<float2*>(slot + tab_bytes());
     double* red = reinterpret_cast<double*>(slot + tab_bytes() + buf_bytes());
 
-    const float4* gtab = A.tables + size_t(ch) * 2 * N;
+    const float4* gtab = A.tables + size_t(ch) * kTabs * 2 * N;
     if constexpr (kTabSmem) {
       for (int i = t; i < 2 * N; i += T) tab[i] = __ldg(gtab + i);
     }
-    const ChannelCoef cf = A.coef[ch];
+    const ChannelCoef cf = A.coef[size_t(ch) * kTabs];
     float2 a[16], b[16];
     float2* e0 = A.e0 + size_t(ch) * N;
     float2* eh = A.eh + size_t(ch) * N;
@@ -229,32 +260,30 @@ struct Resident {
     for (int step = 0; step < A.n_steps; ++step) {
       const float2* crow = A.cfield + size_t(A.z0 + step) * N;
       float2 c[16];
-      if constexpr (kPrefetchC || STRANG) {
+      if constexpr (kPrefetchC || SPLIT != 1) {
 #pragma unroll
         for (int k = 0; k < 16; ++k) c[k] = __ldg(crow + t + T * k);
       }
-      if constexpr (STRANG) couple_row(a, b, c, cf);  // B(dz/2) A(dz) B(dz/2), half-step cf
-
-      fft_fwd(a, b, buf, twr, tw, t, g);
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        float4 pa, pb;
-        if constexpr (kTabSmem) {
-          pa = tab[k * T + t];
-          pb = tab[N + k * T + t];
-        } else {
-          pa = __ldg(gtab + k * T + t);
-          pb = __ldg(gtab + N + k * T + t);
+      if constexpr (SPLIT == 4) {
+        // B(t/2) A(t) B((1-t)/2) A(1-2t) B((1-t)/2) A(t) B(t/2): sub-step j
+        // couples with set 0 (t/2) or 1 ((1-t)/2), then propagates with
+        // table 0 (t dz) or 1 ((1-2t) dz); one copy of the FFT code
+        const ChannelCoef cf1 = A.coef[size_t(ch) * 2 + 1];
+#pragma unroll 1
+        for (int j = 0; j < 3; ++j) {
+          couple_row(a, b, c, j == 0 ? cf : cf1);
+          propagate(a, b, buf, tab, gtab + (j == 1 ? 2 * N : 0), twr, tw, t, g);
         }
-        a[k] = c_mul2(a[k], pa);
-        b[k] = c_mul2(b[k], pb);
-      }
-      fft_inv(a, b, buf, twr, tw, t, g);
-      if constexpr (!kPrefetchC) {
+        couple_row(a, b, c, cf);
+      } else {
+        if constexpr (STRANG) couple_row(a, b, c, cf);  // B(dz/2) A(dz) B(dz/2), half-step cf
+        propagate(a, b, buf, tab, gtab, twr, tw, t, g);
+        if constexpr (!kPrefetchC && SPLIT == 1) {
 #pragma unroll
-        for (int k = 0; k < 16; ++k) c[k] = __ldg(crow + t + T * k);
+          for (int k = 0; k < 16; ++k) c[k] = __ldg(crow + t + T * k);
+        }
+        couple_row(a, b, c, cf);
       }
-      couple_row(a, b, c, cf);
     }
 
     double sa = 0.0, sb = 0.0;

@@ -163,19 +163,30 @@ __global__ void tables_kernel(SetupArgs sa, const double* __restrict__ omega,
   }
   const double cos_a = sqrt(1.0 - s_ratio * s_ratio);  // cos(alpha), Eq. fov3
   const double kdz = k * sa.dz;
-  if (threadIdx.x == 0) coef[ch] = channel_coef(sa, kdz * sa.coupling_frac, cos_a);
-  float4* out = tables + size_t(ch) * 2 * n;
-  for (int p = threadIdx.x; p < n; p += blockDim.x) {
-    const double q = qbin(rev[p], n, sa.dx);
-    const double scale = 1.0 / (double(n) * gain[p]);
-    const int t = p / 16, kk = p % 16;
-    for (int env = 0; env < 2; ++env) {
-      const double Q = env == 0 ? q + half_h : q - half_h;
-      dc P = tilted_propagator(k, Q * Q, sa.dz);
-      P = dscale(P, scale);
-      const float2 hi = to_f2(P);
-      const float2 lo = make_float2(float(P.re - double(hi.x)), float(P.im - double(hi.y)));
-      out[size_t(env) * n + size_t(kk) * T + t] = make_float4(hi.x, hi.y, lo.x, lo.y);
+  // fractions of dz of the propagations (tables) and couplings (coefficient
+  // sets) of Eq. split-op: order 1: (1; 1); order 2: (1; 1/2); order 4:
+  // (t, 1-2t; t/2, (1-t)/2) with t = 1/(2 - 2^(1/3))
+  const double t4 = 1.0 / (2.0 - cbrt(2.0));
+  const int n_sets = sa.split_order == 4 ? 2 : 1;
+  const double pf[2] = {sa.split_order == 4 ? t4 : 1.0, 1.0 - 2.0 * t4};
+  const double cfr[2] = {sa.split_order == 4 ? 0.5 * t4 : (sa.split_order == 2 ? 0.5 : 1.0),
+                         0.5 * (1.0 - t4)};
+  if (threadIdx.x < n_sets)
+    coef[size_t(ch) * n_sets + threadIdx.x] = channel_coef(sa, kdz * cfr[threadIdx.x], cos_a);
+  for (int set = 0; set < n_sets; ++set) {
+    float4* out = tables + (size_t(ch) * n_sets + set) * 2 * n;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+      const double q = qbin(rev[p], n, sa.dx);
+      const double scale = 1.0 / (double(n) * gain[p]);
+      const int t = p / 16, kk = p % 16;
+      for (int env = 0; env < 2; ++env) {
+        const double Q = env == 0 ? q + half_h : q - half_h;
+        dc P = tilted_propagator(k, Q * Q, sa.dz * pf[set]);
+        P = dscale(P, scale);
+        const float2 hi = to_f2(P);
+        const float2 lo = make_float2(float(P.re - double(hi.x)), float(P.im - double(hi.y)));
+        out[size_t(env) * n + size_t(kk) * T + t] = make_float4(hi.x, hi.y, lo.x, lo.y);
+      }
     }
   }
 }

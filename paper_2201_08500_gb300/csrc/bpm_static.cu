@@ -145,6 +145,7 @@ BPM_API bpm_status bpm_run_noalloc(const bpm_grid* grid, int n_channels,
   sa.chihb_im = crystal->chihbar_im;
   sa.zassenhaus = g.zassenhaus ? 1 : 0;
   sa.coupling_frac = 1.0;
+  sa.split_order = 1;
   sa.x_surface = crystal->x_surface;
   sa.x_end = crystal->x_surface + crystal->thickness;
   sa.tan_psi = 0.0;  // symmetric-Bragg slab only on this entry point
@@ -209,7 +210,7 @@ BPM_API bpm_status bpm_run_noalloc(const bpm_grid* grid, int n_channels,
   a.n_ch = n_channels;
   a.z0 = 0;
   a.n_steps = g.nz;
-  a.pre_couple = 0;
+  a.split_order = 1;
   BPM_SCUDA(launch_march(g.nx, 1, n_channels, a, st), "march kernel");
   return BPM_OK;
 }

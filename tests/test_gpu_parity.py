@@ -219,3 +219,39 @@ def test_laue_slab_geometry_matches_oracle(stream):
     g = run_gpu(w, stream)
     e = errors(w, g)
     assert e["per_ch"] < TOL_FIELD and e["relh"] < TOL_FIELD, e
+
+
+@pytest.mark.parametrize("nx", [512, 4096, 8192])
+def test_fourth_order_splitting_matches_oracle(stream, nx):
+    """Fourth-order splitting (Eq. split-op, t = 1/(2 - 2^(1/3))): three
+    propagations and four couplings per step, two table sets per channel."""
+    w = deformed_small(nx, nz=100, n_ch=3, seed=nx + 2)
+    w.split_order = 4
+    g = run_gpu(w, stream)
+    e = errors(w, g)
+    assert e["per_ch"] < TOL_FIELD and e["relh"] < TOL_FIELD, e
+    w2 = deformed_small(nx, nz=100, n_ch=3, seed=nx + 2)
+    w2.split_order = 2
+    g2 = run_gpu(w2, stream)
+    assert np.linalg.norm(g2["eh"] - g["eh"]) > 1e-5 * np.linalg.norm(g["eh"])  # a different scheme
+
+
+def test_fourth_order_grouped_channels_and_batch_refusal(stream):
+    """Several channels per block at N = 512 with a ragged tail; batches refuse
+    fourth-order plans."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    w = deformed_small(512, nz=30, n_ch=8 * sms + 5, seed=12)
+    w.split_order = 4
+    p = bpm.plan_from_workload(w, stream=stream)
+    assert p.stats()["channels_per_block"] == 8
+    p.run()
+    p.sync()
+    g = dict(e0=p.e0(), eh=p.eh())
+    e = errors(w, g, channels=[0, 7, 8, w.n_ch - 1])
+    assert e["per_ch"] < TOL_FIELD, e
+    b = bpm.Batch(stream=stream)
+    with pytest.raises(bpm.BpmError):
+        b.submit(p)
+    b.close()
+    p.close()

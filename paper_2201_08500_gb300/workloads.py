@@ -242,3 +242,43 @@ def large_3d(n_ch: int = 128, nx: int = 512, ny: int = 512, nz: int = 1000, seed
     return Workload(f"large-3d-{nx}x{ny}-nz{nz}-ch{n_ch}", 3, nx, ny, nz, dx, dy, dz, CHI0, CHIH,
                     CHIH, THETA_B, LAMBDA_B, xs, d, u, omega, S, THETA_B, int(80 * s) * dx,
                     int(40 * s) * dx, meta=dict(A=amp, wx=wx, wy=wy, seed=seed))
+
+
+def strain_gradient(B: float = 0.25, beta_ratio: float = 4.7326, depth_um: float = 140.0,
+                    nx: int = 4096, dx: float = 0.25e-6, dz: float = 0.5e-6,
+                    z_end_um: float = 900.0, w0_um: float = 20.0) -> Workload:
+    """Constant strain gradient in a symmetric Bragg crystal (Section 3.2,
+    "Deformed crystals"): Si(444) at 17 keV (lambda = 0.72932 A, d = a/sqrt(48),
+    a = 5.43102 A), absorption and refraction off (chi0 = 0, chi_h real), and
+    displacement u = B x'^2 along h (x' = depth below the entrance surface),
+    the reading of the garbled Eq. Authier2 that reproduces the strain-gradient
+    parameter beta = 4 B sin^2(theta_B) tan(theta_B)/|chi_h| (Eq. Yan).
+    |chi_h| is taken from the paper's printed ratio beta/beta_c, with
+    beta_c = pi/(2 Lambda0) and Lambda0 = lambda cos(theta_B)/|chi_h|:
+    beta/beta_c = 8 B lambda sin^3(theta_B)/(pi |chi_h|^2).
+
+    A single channel at the Bragg wavelength enters at theta_B + 2 B x_r
+    tan(theta_B), so that the local Bragg condition is met x_r = depth_um below
+    the surface, far from both faces of a crystal of thickness x_r + 80 um.
+    The beam starts 60 um in front of the surface; after z_end the transmitted
+    branch has left through the back face and the reflected one through the
+    front face, neither wrapping around the periodic x window.
+    meta: B, beta_ratio, the Landau-Zener fraction exp(-2 pi / beta_ratio) of
+    the new (transmitted) branch, and the x of both faces."""
+    lam = 0.72932e-10
+    theta_b = math.asin(lam / (2.0 * 5.43102e-10 / math.sqrt(48.0)))
+    chih = -math.sqrt(8.0 * B * lam * math.sin(theta_b) ** 3 / (math.pi * beta_ratio))
+    nz = int(round(z_end_um * 1e-6 / dz))
+    xs = 300e-6 + 0.5 * dx
+    thickness = (depth_um + 80.0) * 1e-6
+    x = np.arange(nx, dtype=np.float64) * dx
+    depth = np.clip(x - xs, 0.0, None)
+    u = np.tile(B * depth ** 2, (nz, 1))
+    theta_i = theta_b + 2.0 * B * depth_um * 1e-6 * math.tan(theta_b)
+    omega = np.array([2.0 * math.pi * C_LIGHT / lam])
+    return Workload(f"strain-gradient-B{B}", 2, nx, 1, nz, dx, 0.0, dz, 0j, complex(chih, 0.0),
+                    complex(chih, 0.0), theta_b, lam, xs, thickness, u, omega,
+                    np.ones(1, np.complex128), theta_i, xs - 60e-6, w0_um * 1e-6,
+                    meta=dict(B=B, beta_ratio=beta_ratio,
+                              interbranch=math.exp(-2.0 * math.pi / beta_ratio),
+                              x_front=xs, x_back=xs + thickness))

@@ -255,3 +255,18 @@ def test_fourth_order_grouped_channels_and_batch_refusal(stream):
         b.submit(p)
     b.close()
     p.close()
+
+
+def test_strain_gradient_benchmark(stream):
+    """Section 3.2, constant strain gradient: the CUDA path against the oracle
+    on the Si(444) case (Nx = 4096, 1800 steps), and the fraction of the new
+    branch against exp(-2 pi beta_c/|beta|) = 0.2651 at 1.5e-3 relative."""
+    w = workloads.strain_gradient()
+    g = run_gpu(w, stream)
+    e = errors(w, g)
+    assert e["per_ch"] < TOL_FIELD, e
+    x = np.arange(w.nx) * w.dx
+    inten = np.abs(g["e0"][0]) ** 2 + np.abs(g["eh"][0]) ** 2
+    p0 = np.sum(np.abs(e["init"][0]) ** 2)
+    trans = np.sum(inten[x >= w.meta["x_back"]]) / p0
+    assert abs(trans / w.meta["interbranch"] - 1.0) < 1.5e-3, trans

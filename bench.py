@@ -34,6 +34,12 @@ sys.path.insert(0, ROOT)
 from paper_2201_08500_gb300 import workloads  # noqa: E402
 
 METRIC = "BPM cell-updates/s (omega*x*z)"
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
+# default march, from one ncu capture of that launch (597.55 MB read, 62.88 MB
+# written): the per-launch deformation rows are re-read by each of the ~7
+# waves of channels, which at 9.7 GB/s is immaterial to this ALU-bound kernel.
+# Keyed by kernel and workload; any other configuration reports null.
+MEASURED_TRAFFIC = {("march_kernel<4096,1>", "deformed-2d-nx4096-nz2000-ch1024", 1): 660.43e6}
 UNIT = "cell-updates/s"
 FP32_LANES_PER_SM = 128
 
@@ -533,6 +539,10 @@ def main():
     n = w.nx
     march_avg = statistics.mean(march_ms)
     achieved = cells_per_rank * flops_per_cell(n, w.split_order) / (march_avg * 1e-3) / 1e12
+    # algorithmic DRAM bytes of one launch: tables (32 B per channel and x), fields
+    # in and out (32 B), one read of the deformation rows (8 B per x and step)
+    sets = 2 if w.split_order == 4 else 1
+    alg_bytes = w.n_ch * n * (32 * sets + 32) + w.nz * n * 8
     props = torch.cuda.get_device_properties(local)
     pk = measured_peaks()
     sm_max = pk.get("sm_max_mhz", 2070.0)
@@ -551,7 +561,11 @@ def main():
                        "parallelism": f"{world} x independent instance",
                        "launch": plan.launch(), "tuned": tried},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": MEASURED_TRAFFIC.get(
+                             (f"march_kernel<{n},{st['channels_per_block']}>", w.name,
+                              w.split_order)),
+                         "algorithmic_bytes": alg_bytes,
                          "kernel": f"march_kernel<{n},{st['channels_per_block']}>",
                          "flops_per_cell_update": flops_per_cell(n, w.split_order),
                          "march_ms": march_avg,

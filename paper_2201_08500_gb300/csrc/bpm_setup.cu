@@ -265,12 +265,21 @@ __global__ void incident_kernel(SetupArgs sa, const double* __restrict__ omega,
 // Frequency-to-time, n a power of two: per block COLS columns of the
 // [n][plane] spectrum, FP64 radix-2 transform in shared memory (bit-reversed
 // load, log2 n butterfly passes), output scaled by d_omega exp(2 pi i (n/2) j / n).
+// The n/2 twiddles W^m = exp(-2 pi i m / n) are computed once per block into
+// shared memory; stage len uses W^(kk n / len) (the same double as
+// exp(-2 pi i kk / len): both arguments are exact binary fractions).
 constexpr int kCols = 8;
 __global__ void omega_to_t_fft_kernel(int n, int logn, long long plane, double domega,
                                       const float2* __restrict__ eh, double2* out) {
-  extern __shared__ double2 sm[];  // [n][kCols]
+  extern __shared__ double2 sm[];  // [n][kCols], then the twiddles [n/2]
+  double2* tw = sm + size_t(n) * kCols;
   const long long x0 = (long long)blockIdx.x * kCols;
   const int cols = int(min((long long)kCols, plane - x0));
+  for (int m = threadIdx.x; m < n / 2; m += blockDim.x) {
+    double s, co;
+    sincospi(-2.0 * double(m) / double(n), &s, &co);
+    tw[m] = make_double2(co, s);
+  }
   for (int idx = threadIdx.x; idx < n * kCols; idx += blockDim.x) {
     const int i = idx / kCols, c = idx % kCols;
     const int ri = logn ? int(__brev(unsigned(i)) >> (32 - logn)) : 0;
@@ -284,14 +293,14 @@ __global__ void omega_to_t_fft_kernel(int n, int logn, long long plane, double d
   __syncthreads();
   for (int half = 1; half < n; half <<= 1) {
     const int len = half * 2;
+    const int step = n / len;
     for (int idx = threadIdx.x; idx < (n / 2) * kCols; idx += blockDim.x) {
       const int bf = idx / kCols, c = idx % kCols;
       const int grp = bf / half, kk = bf % half;
       const int ia = grp * len + kk, ib = ia + half;
-      double s, co;
-      sincospi(-2.0 * double(kk) / double(len), &s, &co);
+      const double2 w = tw[kk * step];
       const double2 u = sm[ia * kCols + c], v = sm[ib * kCols + c];
-      const double2 wv = make_double2(v.x * co - v.y * s, v.x * s + v.y * co);
+      const double2 wv = make_double2(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x);
       sm[ia * kCols + c] = make_double2(u.x + wv.x, u.y + wv.y);
       sm[ib * kCols + c] = make_double2(u.x - wv.x, u.y - wv.y);
     }
@@ -301,9 +310,11 @@ __global__ void omega_to_t_fft_kernel(int n, int logn, long long plane, double d
   for (int idx = threadIdx.x; idx < n * kCols; idx += blockDim.x) {
     const int j = idx / kCols, c = idx % kCols;
     if (c >= cols) continue;
-    const long long e = ((long long)ic * j) % n;
-    double s, co;
-    sincospi(2.0 * double(e) / double(n), &s, &co);
+    // exp(+2 pi i e / n) = conj(W^e), W^(e + n/2) = -W^e
+    const int e = int(((long long)ic * j) % n);
+    const double2 w0 = tw[e % ic];
+    const double sg = e < ic ? 1.0 : -1.0;
+    const double co = sg * w0.x, s = -sg * w0.y;
     const double2 v = sm[j * kCols + c];
     out[(long long)j * plane + x0 + c] =
         make_double2(domega * (v.x * co - v.y * s), domega * (v.x * s + v.y * co));
@@ -368,8 +379,8 @@ cudaError_t launch_incident(const SetupArgs& sa, const double* omega, const doub
 cudaError_t launch_omega_to_t(int n_ch, long long plane, double domega, const float2* eh,
                               double2* out, cudaStream_t s) {
   const bool pow2 = n_ch > 0 && (n_ch & (n_ch - 1)) == 0;
-  const size_t smem = size_t(n_ch) * kCols * sizeof(double2);
-  if (pow2 && smem <= 200 * 1024) {
+  const size_t smem = size_t(n_ch) * kCols * sizeof(double2) + size_t(n_ch / 2) * sizeof(double2);
+  if (pow2 && n_ch >= 2 && smem <= 200 * 1024) {
     int logn = 0;
     while ((1 << logn) < n_ch) ++logn;
     const long long blocks = (plane + kCols - 1) / kCols;

@@ -142,15 +142,18 @@ def whole_job_value(world: int, cells_per_rank: int, ms: float) -> float:
     return world * cells_per_rank / (ms * 1e-3)
 
 
-def oracle_sample(w, n_channels: int, n_threads: int):
-    """Time the FP64 oracle (as it stands) on n_channels channels of workload w."""
+def oracle_sample(w, n_channels: int, n_threads: int, keep: bool = False):
+    """Time the FP64 oracle (as it stands) on n_channels channels of workload w
+    spread over the band; keep=True also returns (channel indices, e0, eh, init)."""
     import oracle.oracle as orc
     orc.build()
     idx = np.linspace(0, w.n_ch - 1, n_channels).round().astype(int)
     t0 = time.perf_counter()
-    orc.run(w, channels=idx, n_threads=n_threads)
+    out = orc.run(w, channels=idx, n_threads=n_threads)
     dt = time.perf_counter() - t0
     cells = n_channels * w.plane * w.nz
+    if keep:
+        return cells / dt, dt, cells, (idx,) + tuple(out)
     return cells / dt, dt, cells
 
 
@@ -443,7 +446,7 @@ def main():
                     help="deformed: one instance (default line); batched: 64 uneven instances "
                          "in one work-queue launch vs one launch per instance")
     ap.add_argument("--instances", type=int, default=64)
-    ap.add_argument("--requests", type=int, default=2000,
+    ap.add_argument("--requests", type=int, default=10000,
                     help="served: number of requests (80 % rocking-curve probes)")
     ap.add_argument("--load", type=float, default=0.7, help="served: offered load / capacity")
     args = ap.parse_args()
@@ -580,10 +583,20 @@ def main():
             cores = os.cpu_count() or 1
             # about 10 s of CPU work: 12 channels per core, full march
             n_s = max(1, min(w.n_ch, 12 * cores))
-            v, dt, cells = oracle_sample(w, n_s, cores)
+            v, dt, cells, (idx, o0, oh, init) = oracle_sample(w, n_s, cores, keep=True)
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                     "sample": f"{n_s} of {w.n_ch} channels spread over the band, "
                                               f"full {w.nz}-step march ({dt:.1f} s)"}
+            # error of the GPU's FP32 fields (the last bench step, z = Nz) on the same
+            # channels, per channel relative to the incident field's norm
+            g0, gh = plan.e0()[idx], plan.eh()[idx]
+            inc = np.linalg.norm(init, axis=1)
+            err = np.maximum(np.linalg.norm(g0 - o0, axis=1), np.linalg.norm(gh - oh, axis=1)) / inc
+            line["parity"] = {"vs": "FP64 oracle", "channels": int(n_s),
+                              "max_err_per_channel": float(err.max()),
+                              "median_err_per_channel": float(np.median(err)),
+                              "rel_l2_eh": float(np.linalg.norm(gh - oh) / np.linalg.norm(oh)),
+                              "tolerance": 1e-4}
         print(json.dumps(line), flush=True)
     plan.close()
     if dist is not None:

@@ -7,10 +7,11 @@
 // (T = Nx/16 threads per channel): Nx = 256, 512, 1024, 2048, 4096 pack 16, 8,
 // 4, 2, 1 channels into the 256-thread block, each with its own shared-memory
 // slot (at most 196 KB).  Nx = 8192 needs 512 threads and runs in a sibling
-// kernel of the same structure.  The counter lives in global memory and is
+// kernel of the same structure, with the parked-envelope body (bpm_parked.cuh).  The counter lives in global memory and is
 // cleared before each launch; the queue never waits, so no block can hang.
 #include <cuda_runtime.h>
 
+#include "bpm_parked.cuh"
 #include "bpm_resident.cuh"
 
 namespace bpm {
@@ -68,7 +69,7 @@ __global__ void __launch_bounds__(512, 1)
     const int it = s_item;
     if (it >= n_items) break;
     const BatchItem item = items[it];
-    if (item.n == 8192) Resident<8192, 1, STRANG ? 2 : 1>::run_item(plans[item.plan], item.ch0, smem);
+    if (item.n == 8192) Parked<8192, STRANG ? 2 : 1>::run_item(plans[item.plan], item.ch0, smem);
   }
 }
 
@@ -79,7 +80,7 @@ int batch_group(int n) { return n == 8192 ? 1 : kSmallThreads / (n / 16); }
 cudaError_t launch_batch(const MarchArgs* plans, const BatchItem* items, int n_items, int* counter,
                          bool big, bool strang, int blocks, cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
-  const size_t big_smem = Resident<8192, 1>::smem_bytes();
+  const size_t big_smem = Parked<8192, 1>::smem_bytes();
   if (!big && !strang)
     batch_kernel<false><<<blocks, kSmallThreads, kSmallSmem, s>>>(plans, items, n_items, counter);
   else if (!big)
@@ -92,7 +93,7 @@ cudaError_t launch_batch(const MarchArgs* plans, const BatchItem* items, int n_i
 }
 
 cudaError_t batch_set_attributes() {
-  const int small = int(kSmallSmem), big = int(Resident<8192, 1>::smem_bytes());
+  const int small = int(kSmallSmem), big = int(Parked<8192, 1>::smem_bytes());
   cudaError_t r[] = {
       cudaFuncSetAttribute(batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, small),
       cudaFuncSetAttribute(batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, small),

@@ -16,8 +16,9 @@
 // S-1..0, conjugate twiddle, then the conjugate butterfly), so the forward and
 // inverse twiddle phase errors cancel on the diagonal of every round trip.
 // Between stages the 16 values per thread are exchanged through shared memory
-// at XOR-swizzled addresses p ^ ((p >> 4) & 15), which keeps every 8-byte
-// access of a half-warp on distinct banks for all stages and sizes.
+// (the resident march uses the padded layout of Pad<N>; the 3D passes the
+// XOR swizzle p ^ ((p >> 4) & 15)); both keep every access phase of a warp on
+// distinct banks for all stages and sizes.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -70,6 +71,29 @@ struct Geom {
 };
 
 BPM_DEV int swz(int p) { return p ^ ((p >> 4) & 15); }
+
+// Padded exchange layout of the resident march: position p lives at slot
+// p + p/16 (one spare slot per 16), N + N/16 slots in all.  For every stage s
+// the slot of (t, k) is padbase<s>(t) + padoff<s>(k), a per-thread base plus a
+// compile-time constant (the positions of one thread step by LN(s) in k, and
+// the low four bits of its base are below LN(s) when LN(s) < 16), so an
+// exchange needs one address register per pattern.  Consecutive threads land
+// on distinct banks for 64-bit (16-thread phases) and 128-bit (8-thread
+// phases) accesses at every size and stage.
+template <int N>
+struct Pad {
+  using Gm = Geom<N>;
+  static constexpr int kSlots = N + N / 16;
+  template <int s>
+  static BPM_DEV int base(int t) {
+    const int p = Gm::template pos<s>(t, 0);
+    return p + (p >> 4);
+  }
+  template <int s>
+  __host__ __device__ static constexpr int off(int k) {
+    return s == Gm::S - 1 ? k : Gm::LN(s) * k + ((Gm::LN(s) * k) >> 4);
+  }
+};
 
 // 4-point DFT in place: forward y_m = sum_k v_k exp(-2 pi i k m / 4); INV conjugates.
 template <bool INV>

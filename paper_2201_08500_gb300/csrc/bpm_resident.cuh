@@ -9,6 +9,25 @@
 
 namespace bpm {
 
+// Pointwise two-beam coupling of Eq. fov10 at one crystal cell (|c| = 1):
+//   E0 <- a E0 + b+ c Eh,   Eh <- a Eh + b- conj(c) E0   (pre-update values),
+// with a as FP32 hi + lo.
+BPM_DEV void couple_cell(float2& p, float2& m, float2 c, const ChannelCoef& cf) {
+  const float ahx = cf.a_hi.x, ahy = cf.a_hi.y, alx = cf.a_lo.x, aly = cf.a_lo.y;
+  const float2 bpc = c_mul(cf.bp, c);   // b+ c
+  const float2 bmc = c_mulc(cf.bm, c);  // b- conj(c)
+  const float px = fmaf(ahx, p.x, fmaf(-ahy, p.y, fmaf(bpc.x, m.x, fmaf(-bpc.y, m.y,
+                                                                          fmaf(alx, p.x, -aly * p.y)))));
+  const float py = fmaf(ahx, p.y, fmaf(ahy, p.x, fmaf(bpc.x, m.y, fmaf(bpc.y, m.x,
+                                                                         fmaf(alx, p.y, aly * p.x)))));
+  const float mx = fmaf(ahx, m.x, fmaf(-ahy, m.y, fmaf(bmc.x, p.x, fmaf(-bmc.y, p.y,
+                                                                          fmaf(alx, m.x, -aly * m.y)))));
+  const float my = fmaf(ahx, m.y, fmaf(ahy, m.x, fmaf(bmc.x, p.y, fmaf(bmc.y, p.x,
+                                                                         fmaf(alx, m.y, aly * m.x)))));
+  p = make_float2(px, py);
+  m = make_float2(mx, my);
+}
+
 template <int T, int G>
 BPM_DEV void group_sync(int g) {
   if constexpr (G == 1 && T >= 32) {
@@ -49,7 +68,10 @@ struct Resident {
   static constexpr int kTwSlots = kTwRegs ? (NTW > 0 ? NTW : 1) : 1;
 
   __host__ __device__ static constexpr size_t tab_bytes() { return kTabSmem ? size_t(2) * N * sizeof(float4) : 0; }
-  __host__ __device__ static constexpr size_t buf_bytes() { return size_t(2) * N * sizeof(float2); }
+  static constexpr bool kPadX = L2TAB;  // padded exchange layout (see exchange)
+  __host__ __device__ static constexpr size_t buf_bytes() {
+    return size_t(kPadX ? Pad<N>::kSlots : N) * sizeof(float4);
+  }
   __host__ __device__ static constexpr size_t red_bytes() { return 64 * sizeof(double); }
   __host__ __device__ static constexpr size_t slot_bytes() { return tab_bytes() + buf_bytes() + red_bytes(); }
   __host__ __device__ static constexpr size_t smem_bytes() { return G * slot_bytes(); }
@@ -111,24 +133,41 @@ struct Resident {
 
   // Move both envelopes from the layout of stage SF to that of stage ST.  The
   // two envelopes of a position share one 16-byte slot {E0, Eh}, so each
-  // element costs one 128-bit store and one 128-bit load; with the XOR swizzle
-  // the 8 threads of every 128-bit access phase hit distinct bank groups for
-  // all sizes and stages.
+  // element costs one 128-bit store and one 128-bit load.  The 128-register
+  // L2 form uses the padded layout (Pad<N>: one base register per pattern,
+  // constant offsets); the shared-memory form, with registers to spare, the
+  // XOR swizzle, which measured faster there.  Both are free of bank conflicts
+  // for 8-thread 128-bit phases at every size and stage.
   template <int SF, int ST>
   static BPM_DEV void exchange(float2 (&a)[16], float2 (&b)[16], float2* buf, int t, int g) {
     float4* b4 = reinterpret_cast<float4*>(buf);
-    group_sync<T, G>(g);
+    if constexpr (kPadX) {
+      using P = Pad<N>;
+      float4* st = b4 + P::template base<SF>(t);
+      const float4* ld = b4 + P::template base<ST>(t);
+      group_sync<T, G>(g);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const int p = swz(Gm::template pos<SF>(t, k));
-      b4[p] = make_float4(a[k].x, a[k].y, b[k].x, b[k].y);
-    }
-    group_sync<T, G>(g);
+      for (int k = 0; k < 16; ++k)
+        st[P::template off<SF>(k)] = make_float4(a[k].x, a[k].y, b[k].x, b[k].y);
+      group_sync<T, G>(g);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const float4 v = b4[swz(Gm::template pos<ST>(t, k))];
-      a[k] = make_float2(v.x, v.y);
-      b[k] = make_float2(v.z, v.w);
+      for (int k = 0; k < 16; ++k) {
+        const float4 v = ld[P::template off<ST>(k)];
+        a[k] = make_float2(v.x, v.y);
+        b[k] = make_float2(v.z, v.w);
+      }
+    } else {
+      group_sync<T, G>(g);
+#pragma unroll
+      for (int k = 0; k < 16; ++k)
+        b4[swz(Gm::template pos<SF>(t, k))] = make_float4(a[k].x, a[k].y, b[k].x, b[k].y);
+      group_sync<T, G>(g);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const float4 v = b4[swz(Gm::template pos<ST>(t, k))];
+        a[k] = make_float2(v.x, v.y);
+        b[k] = make_float2(v.z, v.w);
+      }
     }
   }
 
@@ -169,19 +208,7 @@ struct Resident {
 
   // Pointwise two-beam coupling of Eq. fov10 at one crystal cell (|c| = 1).
   static BPM_DEV void couple_in(float2& p, float2& m, float2 c, const ChannelCoef& cf) {
-    const float ahx = cf.a_hi.x, ahy = cf.a_hi.y, alx = cf.a_lo.x, aly = cf.a_lo.y;
-    const float2 bpc = c_mul(cf.bp, c);   // b+ c
-    const float2 bmc = c_mulc(cf.bm, c);  // b- conj(c)
-    const float px = fmaf(ahx, p.x, fmaf(-ahy, p.y, fmaf(bpc.x, m.x, fmaf(-bpc.y, m.y,
-                                                                            fmaf(alx, p.x, -aly * p.y)))));
-    const float py = fmaf(ahx, p.y, fmaf(ahy, p.x, fmaf(bpc.x, m.y, fmaf(bpc.y, m.x,
-                                                                           fmaf(alx, p.y, aly * p.x)))));
-    const float mx = fmaf(ahx, m.x, fmaf(-ahy, m.y, fmaf(bmc.x, p.x, fmaf(-bmc.y, p.y,
-                                                                            fmaf(alx, m.x, -aly * m.y)))));
-    const float my = fmaf(ahx, m.y, fmaf(ahy, m.x, fmaf(bmc.x, p.y, fmaf(bmc.y, p.x,
-                                                                           fmaf(alx, m.y, aly * m.x)))));
-    p = make_float2(px, py);
-    m = make_float2(mx, my);
+    couple_cell(p, m, c, cf);
   }
 
   // Coupling of this thread's 16 cells.  c = 0 marks vacuum (Pi = 0), where the

@@ -205,7 +205,7 @@ def run_batched(args, world, rank, local):
     for w in ws:
         key = (w.nx, w.n_ch)
         if key not in tuned:
-            tuned[key] = bpm.tune(w.dims, w.nx, w.ny, w.dx, w.dy, w.dz, w.n_ch, steps=8)[0]
+            tuned[key] = bpm.tune(w.dims, w.nx, w.ny, w.dx, w.dy, w.dz, w.n_ch, steps=256)[0]
     plans = [bpm.plan_from_workload(w, stream=stream, u=u) for w, u in zip(ws, us)]
     cells = sum(w.cell_updates for w in ws)
     b = bpm.Batch(stream=stream)
@@ -283,7 +283,7 @@ def run_3d(args, world, rank, local):
     w.u = None
     stream = torch.cuda.current_stream()
     # launch form chosen by the autotuner (untimed setup): row-pass tile height
-    tuned, tried = bpm.tune(w.dims, w.nx, w.ny, w.dx, w.dy, w.dz, w.n_ch, steps=8)
+    tuned, tried = bpm.tune(w.dims, w.nx, w.ny, w.dx, w.dy, w.dz, w.n_ch, steps=32)
     plan = bpm.Plan(w.dims, w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.n_ch, stream=stream)
     plan.set_timing(True)
 
@@ -440,6 +440,9 @@ def main():
                     help="channels of the deformed workload (profiling: a smaller instance)")
     ap.add_argument("--nz", type=int, default=2000, help="z steps of the deformed workload")
     ap.add_argument("--nx", type=int, default=4096, help="transform size of the deformed workload")
+    ap.add_argument("--launch-form", type=int, default=None, choices=[0, 1, 2],
+                    help="force a launch form of the deformed workload's march (default: "
+                         "the autotuner's choice)")
     ap.add_argument("--split-order", type=int, default=1, choices=[1, 2, 4],
                     help="operator splitting of the deformed workload (Eq. split-op)")
     ap.add_argument("--workload", default="deformed", choices=["deformed", "batched", "served", "3d"],
@@ -479,11 +482,16 @@ def main():
     stream = torch.cuda.current_stream()
     u_dev = torch.from_numpy(np.ascontiguousarray(w.u)).cuda()
     # launch form chosen by the autotuner (untimed setup)
+    # (256 steps: short runs over-weight the one-time per-channel table copy of
+    # the shared-memory form)
     _, tried = bpm.tune(w.dims, w.nx, w.ny, w.dx, w.dy, w.dz, w.n_ch,
-                        split_order=w.split_order, steps=16)
+                        split_order=w.split_order, steps=min(w.nz, 256))
     plan = bpm.Plan(w.dims, w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.n_ch, stream=stream,
                     zassenhaus=w.zassenhaus, split_order=w.split_order)
     plan.set_timing(True)
+    if args.launch_form is not None:
+        plan.set_launch(form=args.launch_form,
+                        channels_per_block=1 if args.launch_form == 2 else None)
     omega = np.ascontiguousarray(w.omega)
     S = np.ascontiguousarray(w.S)
 

@@ -190,7 +190,11 @@ BPM_API bpm_status bpm_get_stats(bpm_plan plan, bpm_stats* out);
  *                      twiddles in registers, one channel group per SM;
  *                      1 = tables and twiddles read from L2, at most 128
  *                      registers, two channel groups per SM (first order,
- *                      Nx <= 4096, channels_per_block = the size's maximum).
+ *                      Nx <= 4096, channels_per_block = the size's maximum);
+ *                      2 = parked: one envelope in registers, the other in
+ *                      shared memory, tables and twiddles from L2, one channel
+ *                      per block and 512/(Nx/16) blocks per SM (first order,
+ *                      Nx = 1024, 2048, 4096, channels_per_block = 1).
  *   channels_per_block 2D march: 1, or the maximum of the size (16, 8, 4, 2, 1
  *                      for Nx = 256, 512, 1024, 2048, >= 4096).
  *   row_threads        3D row pass: 256 or 512 threads per block, i.e. a tile
@@ -219,6 +223,8 @@ BPM_API bpm_status bpm_set_launch(bpm_plan plan, const bpm_launch* form);
  * plans of the same (dims, nx, ny, split_order, n_channels) in this process.
  * best receives the fastest; all (capacity max_all, may be NULL) receives every
  * measured form, and n_all their count.  Runs on its own stream and waits for it.
+ * Use a few hundred steps: short runs over-weight one-time costs (the
+ * shared-memory form copies each channel's tables once per launch).
  * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
 BPM_API bpm_status bpm_tune(const bpm_grid* grid, int n_channels, int steps, bpm_launch* best,
                             bpm_launch* all, int max_all, int* n_all);

@@ -173,6 +173,7 @@ const DeviceInfo& device_info() {
     d.ok = true;
     if (d.cc == 103)
       d.ok = march_set_attributes() == cudaSuccess && march_set_attributes_l2() == cudaSuccess &&
+             march_set_attributes_parked() == cudaSuccess &&
              batch_set_attributes() == cudaSuccess &&
              setup_set_attributes() == cudaSuccess && pass3d_set_attributes() == cudaSuccess;
   }
@@ -306,6 +307,7 @@ bool launch_valid(const bpm_grid& g, int form, int group, int row_threads) {
   const int maxg = march_max_group(g.nx);
   if (row_threads != 256) return false;
   if (form == 0) return group == 1 || group == maxg;
+  if (form == 2) return group == 1 && g.split_order == 1 && march_parked_supported(g.nx);
   return form == 1 && g.split_order == 1 && march_l2_supported(g.nx, group);
 }
 
@@ -315,8 +317,9 @@ void apply_launch(bpm_plan p) {
   p->stats.threads_per_channel = march_threads_per_channel(p->grid.nx);
   p->stats.channels_per_block = p->group;
   p->stats.blocks = p->blocks;
-  p->stats.smem_bytes = int(p->form == 1 ? march_l2_smem_bytes(p->grid.nx, p->group)
-                                         : march_smem_bytes(p->grid.nx, p->group));
+  p->stats.smem_bytes = int(p->form == 1   ? march_l2_smem_bytes(p->grid.nx, p->group)
+                            : p->form == 2 ? march_parked_smem_bytes(p->grid.nx)
+                                           : march_smem_bytes(p->grid.nx, p->group));
 }
 
 size_t plan_bytes(const bpm_grid& g, int n_ch) {
@@ -665,6 +668,8 @@ BPM_API bpm_status bpm_run(bpm_plan p, int n_steps) {
   if (p->grid.dims == 2) {
     if (p->form == 1 && a.split_order == 1)
       BPM_CUDA(p, launch_march_l2(p->grid.nx, p->group, p->blocks, a, p->stream), "march kernel");
+    else if (p->form == 2 && a.split_order == 1)
+      BPM_CUDA(p, launch_march_parked(p->grid.nx, p->blocks, a, p->stream), "march kernel");
     else
       BPM_CUDA(p, launch_march(p->grid.nx, p->group, p->blocks, a, p->stream), "march kernel");
     march_launches = 1;
@@ -897,6 +902,7 @@ BPM_API bpm_status bpm_tune(const bpm_grid* grid, int n_channels, int steps, bpm
       cand.push_back(bpm_launch{0, 1, 256, 0.f});
       if (maxg > 1) cand.push_back(bpm_launch{0, maxg, 256, 0.f});
       if (launch_valid(g, 1, maxg, 256)) cand.push_back(bpm_launch{1, maxg, 256, 0.f});
+      if (launch_valid(g, 2, 1, 256)) cand.push_back(bpm_launch{2, 1, 256, 0.f});
     }
     for (size_t i = 0; st == BPM_OK && i < cand.size(); ++i) {
       st = bpm_set_launch(p, &cand[i]);

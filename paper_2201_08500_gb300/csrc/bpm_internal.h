@@ -106,6 +106,12 @@ bool march_l2_supported(int n, int group);
 size_t march_l2_smem_bytes(int n, int group);
 cudaError_t launch_march_l2(int n, int group, int blocks, const MarchArgs& a, cudaStream_t s);
 cudaError_t march_set_attributes_l2();
+// Parked form (one envelope in registers, one in shared memory) at Nx = 1024..4096:
+// one channel per block, several blocks per SM.
+bool march_parked_supported(int n);
+size_t march_parked_smem_bytes(int n);
+cudaError_t launch_march_parked(int n, int blocks, const MarchArgs& a, cudaStream_t s);
+cudaError_t march_set_attributes_parked();
 cudaError_t march_set_attributes_strang();
 // Fourth-order splitting (Eq. split-op, a = (0, t, 1-2t, t), b = (t/2, (1-t)/2, (1-t)/2, t/2)).
 cudaError_t launch_march_split4(int n, int group, int blocks, const MarchArgs& a, cudaStream_t s);

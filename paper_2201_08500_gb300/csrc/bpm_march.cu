@@ -39,7 +39,7 @@ int march_max_group(int n) {
 
 size_t march_smem_bytes(int n, int group) {
 #define BPM_SMEM_CASE(NN, GG) \
-  if (n == NN && group == GG) return MarchBody<NN, GG, 1, false>::type::smem_bytes();
+  if (n == NN && group == GG) return MarchBody<NN, GG, 1, 0>::type::smem_bytes();
   BPM_SMEM_CASE(256, 1) BPM_SMEM_CASE(256, 16)
   BPM_SMEM_CASE(512, 1) BPM_SMEM_CASE(512, 8)
   BPM_SMEM_CASE(1024, 1) BPM_SMEM_CASE(1024, 4)

@@ -10,37 +10,48 @@
 
 namespace bpm {
 
-// Per-channel march body of a launch form: the register-resident form for
-// N <= 4096, the parked-envelope form for N = 8192.
-template <int N, int G, int SPLIT, bool L2TAB>
+// Per-channel march body of a launch form: FORM 0 the register-resident form
+// for N <= 4096 and the parked-envelope form for N = 8192; FORM 1 the L2-table
+// resident form; FORM 2 the parked form at N <= 4096.
+template <int N, int G, int SPLIT, int FORM>
 struct MarchBody {
-  using type = Resident<N, G, SPLIT, L2TAB>;
+  using type = Resident<N, G, SPLIT, FORM == 1>;
 };
 template <int SPLIT>
-struct MarchBody<8192, 1, SPLIT, false> {
+struct MarchBody<8192, 1, SPLIT, 0> {
   using type = Parked<8192, SPLIT>;
 };
+template <int N, int SPLIT>
+struct MarchBody<N, 1, SPLIT, 2> {
+  using type = Parked<N, SPLIT>;
+};
+
+// Resident blocks per SM the form is compiled for (128 registers unless 1).
+__host__ __device__ constexpr int march_min_blocks(int n, int g, int form) {
+  return form == 1 ? 2 : form == 2 ? 512 / (n / 16 * g) : 1;
+}
 
 namespace {
 
-template <int N, int G, int SPLIT, bool L2TAB = false>
-__global__ void __launch_bounds__((N / 16) * G, L2TAB ? 2 : 1) march_kernel(MarchArgs A) {
+template <int N, int G, int SPLIT, int FORM = 0>
+__global__ void __launch_bounds__((N / 16) * G, march_min_blocks(N, G, FORM))
+    march_kernel(MarchArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
-  MarchBody<N, G, SPLIT, L2TAB>::type::run(A, smem);
+  MarchBody<N, G, SPLIT, FORM>::type::run(A, smem);
 }
 
-template <int N, int G, int SPLIT, bool L2TAB = false>
+template <int N, int G, int SPLIT, int FORM = 0>
 cudaError_t launch_one(int blocks, const MarchArgs& a, cudaStream_t s) {
-  march_kernel<N, G, SPLIT, L2TAB>
-      <<<blocks, (N / 16) * G, MarchBody<N, G, SPLIT, L2TAB>::type::smem_bytes(), s>>>(a);
+  march_kernel<N, G, SPLIT, FORM>
+      <<<blocks, (N / 16) * G, MarchBody<N, G, SPLIT, FORM>::type::smem_bytes(), s>>>(a);
   return cudaGetLastError();
 }
 
-template <int N, int G, int SPLIT, bool L2TAB = false>
+template <int N, int G, int SPLIT, int FORM = 0>
 cudaError_t attr_one() {
-  return cudaFuncSetAttribute(march_kernel<N, G, SPLIT, L2TAB>,
+  return cudaFuncSetAttribute(march_kernel<N, G, SPLIT, FORM>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(MarchBody<N, G, SPLIT, L2TAB>::type::smem_bytes()));
+                              int(MarchBody<N, G, SPLIT, FORM>::type::smem_bytes()));
 }
 
 }  // namespace

@@ -9,7 +9,7 @@ namespace bpm {
 
 size_t march_split4_smem_bytes(int n, int group) {
 #define BPM_S4_SMEM(NN, GG) \
-  if (n == NN && group == GG) return MarchBody<NN, GG, 4, false>::type::smem_bytes();
+  if (n == NN && group == GG) return MarchBody<NN, GG, 4, 0>::type::smem_bytes();
   BPM_S4_SMEM(256, 1) BPM_S4_SMEM(256, 16) BPM_S4_SMEM(512, 1) BPM_S4_SMEM(512, 8)
   BPM_S4_SMEM(1024, 1) BPM_S4_SMEM(1024, 4) BPM_S4_SMEM(2048, 1) BPM_S4_SMEM(2048, 2)
   BPM_S4_SMEM(4096, 1) BPM_S4_SMEM(8192, 1)

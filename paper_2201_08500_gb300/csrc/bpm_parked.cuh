@@ -1,8 +1,13 @@
-// Resident march for Nx = 8192 with one envelope parked in shared memory.
+// Resident march with one envelope parked in shared memory: the form of
+// Nx = 8192, and the "parked" launch form of Nx = 1024..4096.
 //
-// One channel per 512-thread block (T = N/16 threads, 16 positions each).  With
-// both envelopes in registers the step needs more than the 128 registers a
-// 512-thread block allows, and the spills went to DRAM.  Here only one
+// One channel per block of T = N/16 threads (16 positions each).  At Nx = 8192
+// both envelopes in registers need more than the 128 registers a 512-thread
+// block allows, and the spills went to DRAM.  At Nx <= 4096, with tables and
+// twiddles read from L2, the parked form needs at most 128 registers and
+// N (1 + 1/16 + 2) complex64 of shared memory (98 KB at 4096), so that two or
+// more channel blocks share an SM and run their exchanges and butterflies at
+// independent phases.  Here only one
 // envelope lives in registers at a time: the other is parked in shared memory
 // at the thread's own x positions (thread-private, so parking needs no
 // barrier), and the two envelopes run the same single-envelope transform one
@@ -90,18 +95,22 @@ struct Parked {
   // propagator (hi + lo table gt of this envelope), inverse FFT.
   static BPM_DEV void propagate(float2 (&v)[16], float2* x, const float4* gt, const float2* tw,
                                 int t) {
-    static_assert(S == 4, "parked form: four stages");
+    static_assert(S == 3 || S == 4, "parked form: 1024 <= N <= 8192");
     stage_fwd<0>(v, tw, t);
     exchange<0, 1>(v, x, t);
     stage_fwd<1>(v, tw, t);
     exchange<1, 2>(v, x, t);
     stage_fwd<2>(v, tw, t);
-    exchange<2, 3>(v, x, t);
-    stage_fwd<3>(v, tw, t);
+    if constexpr (S == 4) {
+      exchange<2, 3>(v, x, t);
+      stage_fwd<3>(v, tw, t);
+    }
 #pragma unroll
     for (int k = 0; k < 16; ++k) v[k] = c_mul2(v[k], __ldg(gt + k * T + t));
-    stage_inv<3>(v, tw, t);
-    exchange<3, 2>(v, x, t);
+    if constexpr (S == 4) {
+      stage_inv<3>(v, tw, t);
+      exchange<3, 2>(v, x, t);
+    }
     stage_inv<2>(v, tw, t);
     exchange<2, 1>(v, x, t);
     stage_inv<1>(v, tw, t);

@@ -38,7 +38,8 @@ def test_every_2d_form_gives_identical_fields(nx, n_ch):
     w = deformed_small(nx, nz=48, n_ch=n_ch, seed=31)
     maxg = {1024: 4, 4096: 1}[nx]
     ref, _ = fields(w, form=0, channels_per_block=1)
-    forms = [dict(form=0, channels_per_block=maxg), dict(form=1, channels_per_block=maxg)]
+    forms = [dict(form=0, channels_per_block=maxg), dict(form=1, channels_per_block=maxg),
+             dict(form=2, channels_per_block=1)]
     for f in forms:
         got, used = fields(w, **f)
         assert used["form"] == f["form"] and used["channels_per_block"] == f["channels_per_block"]
@@ -69,6 +70,8 @@ def test_forms_a_plan_cannot_run_are_refused():
     q = bpm.plan_from_workload(w)
     with pytest.raises(bpm.BpmError):
         q.set_launch(form=1, channels_per_block=16)  # the L2 form is first order only
+    with pytest.raises(bpm.BpmError):
+        q.set_launch(form=2, channels_per_block=1)   # so is the parked form (and Nx >= 1024)
     q.close()
 
 
@@ -76,7 +79,7 @@ def test_tuner_keeps_the_fastest_and_later_plans_use_it(tmp_path):
     bpm.tune_clear()
     dx = 0.5e-6
     best, every = bpm.tune(2, 1024, 1, dx, 0.0, dx, 611, steps=8)
-    assert len(every) == 3 and all(f["ms"] > 0 for f in every)
+    assert len(every) == 4 and all(f["ms"] > 0 for f in every)  # smem x2, L2, parked
     assert best["ms"] == min(f["ms"] for f in every)
     want = {k: best[k] for k in ("form", "channels_per_block", "row_threads")}
     p = bpm.Plan(2, 1024, 1, 30, dx, 0.0, dx, 611)

@@ -440,7 +440,7 @@ def main():
                     help="channels of the deformed workload (profiling: a smaller instance)")
     ap.add_argument("--nz", type=int, default=2000, help="z steps of the deformed workload")
     ap.add_argument("--nx", type=int, default=4096, help="transform size of the deformed workload")
-    ap.add_argument("--launch-form", type=int, default=None, choices=[0, 1, 2],
+    ap.add_argument("--launch-form", type=int, default=None, choices=[0, 1, 2, 3],
                     help="force a launch form of the deformed workload's march (default: "
                          "the autotuner's choice)")
     ap.add_argument("--split-order", type=int, default=1, choices=[1, 2, 4],
@@ -491,7 +491,7 @@ def main():
     plan.set_timing(True)
     if args.launch_form is not None:
         plan.set_launch(form=args.launch_form,
-                        channels_per_block=1 if args.launch_form == 2 else None)
+                        channels_per_block=1 if args.launch_form >= 2 else None)
     omega = np.ascontiguousarray(w.omega)
     S = np.ascontiguousarray(w.S)
 

@@ -307,7 +307,8 @@ bool launch_valid(const bpm_grid& g, int form, int group, int row_threads) {
   const int maxg = march_max_group(g.nx);
   if (row_threads != 256) return false;
   if (form == 0) return group == 1 || group == maxg;
-  if (form == 2) return group == 1 && g.split_order == 1 && march_parked_supported(g.nx);
+  if (form == 2 || form == 3)
+    return group == 1 && g.split_order == 1 && march_parked_supported(g.nx, form);
   return form == 1 && g.split_order == 1 && march_l2_supported(g.nx, group);
 }
 
@@ -318,7 +319,7 @@ void apply_launch(bpm_plan p) {
   p->stats.channels_per_block = p->group;
   p->stats.blocks = p->blocks;
   p->stats.smem_bytes = int(p->form == 1   ? march_l2_smem_bytes(p->grid.nx, p->group)
-                            : p->form == 2 ? march_parked_smem_bytes(p->grid.nx)
+                            : p->form >= 2 ? march_parked_smem_bytes(p->grid.nx)
                                            : march_smem_bytes(p->grid.nx, p->group));
 }
 
@@ -668,8 +669,9 @@ BPM_API bpm_status bpm_run(bpm_plan p, int n_steps) {
   if (p->grid.dims == 2) {
     if (p->form == 1 && a.split_order == 1)
       BPM_CUDA(p, launch_march_l2(p->grid.nx, p->group, p->blocks, a, p->stream), "march kernel");
-    else if (p->form == 2 && a.split_order == 1)
-      BPM_CUDA(p, launch_march_parked(p->grid.nx, p->blocks, a, p->stream), "march kernel");
+    else if (p->form >= 2 && a.split_order == 1)
+      BPM_CUDA(p, launch_march_parked(p->grid.nx, p->form, p->blocks, a, p->stream),
+               "march kernel");
     else
       BPM_CUDA(p, launch_march(p->grid.nx, p->group, p->blocks, a, p->stream), "march kernel");
     march_launches = 1;
@@ -903,6 +905,7 @@ BPM_API bpm_status bpm_tune(const bpm_grid* grid, int n_channels, int steps, bpm
       if (maxg > 1) cand.push_back(bpm_launch{0, maxg, 256, 0.f});
       if (launch_valid(g, 1, maxg, 256)) cand.push_back(bpm_launch{1, maxg, 256, 0.f});
       if (launch_valid(g, 2, 1, 256)) cand.push_back(bpm_launch{2, 1, 256, 0.f});
+      if (launch_valid(g, 3, 1, 256)) cand.push_back(bpm_launch{3, 1, 256, 0.f});
     }
     for (size_t i = 0; st == BPM_OK && i < cand.size(); ++i) {
       st = bpm_set_launch(p, &cand[i]);

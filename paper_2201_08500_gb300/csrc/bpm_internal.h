@@ -108,9 +108,11 @@ cudaError_t launch_march_l2(int n, int group, int blocks, const MarchArgs& a, cu
 cudaError_t march_set_attributes_l2();
 // Parked form (one envelope in registers, one in shared memory) at Nx = 1024..4096:
 // one channel per block, several blocks per SM.
-bool march_parked_supported(int n);
+// (form 2: tables from L2, Nx = 1024..4096; form 3: tables in tensor memory,
+// Nx = 2048..8192).
+bool march_parked_supported(int n, int form);
 size_t march_parked_smem_bytes(int n);
-cudaError_t launch_march_parked(int n, int blocks, const MarchArgs& a, cudaStream_t s);
+cudaError_t launch_march_parked(int n, int form, int blocks, const MarchArgs& a, cudaStream_t s);
 cudaError_t march_set_attributes_parked();
 cudaError_t march_set_attributes_strang();
 // Fourth-order splitting (Eq. split-op, a = (0, t, 1-2t, t), b = (t/2, (1-t)/2, (1-t)/2, t/2)).

@@ -12,7 +12,8 @@ namespace bpm {
 
 // Per-channel march body of a launch form: FORM 0 the register-resident form
 // for N <= 4096 and the parked-envelope form for N = 8192; FORM 1 the L2-table
-// resident form; FORM 2 the parked form at N <= 4096.
+// resident form; FORM 2 the parked form at N <= 4096; FORM 3 the parked form
+// with the tables in tensor memory.
 template <int N, int G, int SPLIT, int FORM>
 struct MarchBody {
   using type = Resident<N, G, SPLIT, FORM == 1>;
@@ -25,10 +26,14 @@ template <int N, int SPLIT>
 struct MarchBody<N, 1, SPLIT, 2> {
   using type = Parked<N, SPLIT>;
 };
+template <int N, int SPLIT>
+struct MarchBody<N, 1, SPLIT, 3> {
+  using type = Parked<N, SPLIT, true>;
+};
 
 // Resident blocks per SM the form is compiled for (128 registers unless 1).
 __host__ __device__ constexpr int march_min_blocks(int n, int g, int form) {
-  return form == 1 ? 2 : form == 2 ? 512 / (n / 16 * g) : 1;
+  return form == 1 ? 2 : (form == 2 || form == 3) ? 512 / (n / 16 * g) : 1;
 }
 
 namespace {

@@ -27,16 +27,24 @@
 #include <cuda_runtime.h>
 
 #include "bpm_resident.cuh"
+#include "bpm_tmem.cuh"
 
 namespace bpm {
 
-template <int N, int SPLIT = 1>
+// TMEM = true keeps each thread's propagator-table slice in tensor memory
+// (bpm_tmem.cuh, 128 columns per thread: 2 envelopes x 16 positions x hi/lo
+// float4) instead of reading it from L2 every step (one table set: SPLIT 1, 2).
+template <int N, int SPLIT = 1, bool TMEM = false>
 struct Parked {
   static_assert(SPLIT == 1 || SPLIT == 2 || SPLIT == 4, "splitting order");
+  static_assert(!TMEM || SPLIT != 4, "TMEM tables: one table set");
   using Gm = Geom<N>;
   static constexpr int T = Gm::T;
   static constexpr int S = Gm::S;
   static constexpr int kTabs = SPLIT == 4 ? 2 : 1;
+  // TMEM columns of the block: warps w and w + 4 share lanes, so each group of
+  // four warps takes its own 128 columns
+  static constexpr int kCols = 128 * (T >= 128 ? T / 128 : 1);
 
   __host__ __device__ static constexpr size_t xbuf_bytes() { return size_t(Pad<N>::kSlots) * sizeof(float2); }
   __host__ __device__ static constexpr size_t vec_bytes() { return size_t(N) * sizeof(float2); }
@@ -93,8 +101,26 @@ struct Parked {
 
   // One envelope: forward FFT, digit-reversed spectrum times the tilted
   // propagator (hi + lo table gt of this envelope), inverse FFT.
-  static BPM_DEV void propagate(float2 (&v)[16], float2* x, const float4* gt, const float2* tw,
-                                int t) {
+  // Table multiply of one envelope: 16 positions, hi/lo float4 each, from L2
+  // (gt) or from this thread's TMEM columns (tcol).
+  static BPM_DEV void multiply(float2 (&v)[16], const float4* gt, uint32_t tcol, int t) {
+    if constexpr (TMEM) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float4 tv[4];
+        tmem_ld16(tcol + uint32_t(16 * c), tv);
+        tmem_wait_ld();
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[4 * c + i] = c_mul2(v[4 * c + i], tv[i]);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) v[k] = c_mul2(v[k], __ldg(gt + k * T + t));
+    }
+  }
+
+  static BPM_DEV void propagate(float2 (&v)[16], float2* x, const float4* gt, uint32_t tcol,
+                                const float2* tw, int t) {
     static_assert(S == 3 || S == 4, "parked form: 1024 <= N <= 8192");
     stage_fwd<0>(v, tw, t);
     exchange<0, 1>(v, x, t);
@@ -105,8 +131,7 @@ struct Parked {
       exchange<2, 3>(v, x, t);
       stage_fwd<3>(v, tw, t);
     }
-#pragma unroll
-    for (int k = 0; k < 16; ++k) v[k] = c_mul2(v[k], __ldg(gt + k * T + t));
+    multiply(v, gt, tcol, t);
     if constexpr (S == 4) {
       stage_inv<3>(v, tw, t);
       exchange<3, 2>(v, x, t);
@@ -120,14 +145,14 @@ struct Parked {
 
   // [E0 in v, Eh parked] -> [Eh in v, E0 parked], both propagated (table set gt).
   static BPM_DEV void propagate_both(float2 (&v)[16], float2* x, float2* p0, float2* ph,
-                                     const float4* gt, const float2* tw, int t) {
-    propagate(v, x, gt, tw, t);
+                                     const float4* gt, uint32_t tcol, const float2* tw, int t) {
+    propagate(v, x, gt, tcol, tw, t);
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
       p0[k * T + t] = v[k];
       v[k] = ph[k * T + t];
     }
-    propagate(v, x, gt + N, tw, t);
+    propagate(v, x, gt + N, tcol + 64u, tw, t);
   }
 
   // [Eh in v, E0 parked] -> coupling at z_n -> [E0 in v, Eh parked].
@@ -157,8 +182,30 @@ struct Parked {
     }
   }
 
+  // This thread's TMEM address: lanes of its warp's quarter, its warp group's
+  // 128 columns (envelope e, position k at columns 64 e + 4 k .. + 3).
+  static BPM_DEV uint32_t tmem_thread(uint32_t tbase, int t) {
+    const int w = t / 32;
+    return tbase + (uint32_t(32 * (w % 4)) << 16) + uint32_t(128 * (w / 4));
+  }
+
+  // Copies channel ch's tables (one set) from L2 into this thread's columns.
+  static BPM_DEV void tmem_fill(const float4* gtab, uint32_t tcol, int t) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float4 tv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) tv[i] = __ldg(gtab + e * N + (4 * c + i) * T + t);
+        tmem_st16(tcol + uint32_t(64 * e + 16 * c), tv);
+      }
+    tmem_wait_st();
+  }
+
   // March channel ch of plan A by A.n_steps steps (this block: T threads).
-  static BPM_DEV void march_channel(const MarchArgs& A, int ch, unsigned char* smem, int t) {
+  static BPM_DEV void march_channel(const MarchArgs& A, int ch, unsigned char* smem, int t,
+                                    uint32_t tcol = 0) {
     float2* x = reinterpret_cast<float2*>(smem);
     float2* p0 = x + Pad<N>::kSlots;
     float2* ph = p0 + N;
@@ -168,6 +215,7 @@ struct Parked {
     const float2* tw = A.twiddle_t;
     float2* e0 = A.e0 + size_t(ch) * N;
     float2* eh = A.eh + size_t(ch) * N;
+    if constexpr (TMEM) tmem_fill(gtab, tcol, t);
     float2 v[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
@@ -181,12 +229,12 @@ struct Parked {
         couple_front(v, ph, crow, cf, t);
 #pragma unroll 1
         for (int j = 0; j < 3; ++j) {
-          propagate_both(v, x, p0, ph, gtab + (j == 1 ? 2 * N : 0), tw, t);
+          propagate_both(v, x, p0, ph, gtab + (j == 1 ? 2 * N : 0), tcol, tw, t);
           couple_back(v, p0, ph, crow, j == 2 ? cf : cf1, t);
         }
       } else {
         if constexpr (SPLIT == 2) couple_front(v, ph, crow, cf, t);
-        propagate_both(v, x, p0, ph, gtab, tw, t);
+        propagate_both(v, x, p0, ph, gtab, tcol, tw, t);
         couple_back(v, p0, ph, crow, cf, t);
       }
     }
@@ -225,11 +273,23 @@ struct Parked {
   }
 
   static BPM_DEV void run(const MarchArgs& A, unsigned char* smem) {
-    for (int ch = blockIdx.x; ch < A.n_ch; ch += gridDim.x)
-      march_channel(A, ch, smem, threadIdx.x);
+    const int t = threadIdx.x;
+    if constexpr (TMEM) {
+      __shared__ uint32_t s_tbase;
+      if (t / 32 == 0) tmem_alloc<kCols>(&s_tbase);
+      tmem_sync();
+      const uint32_t tbase = s_tbase;
+      for (int ch = blockIdx.x; ch < A.n_ch; ch += gridDim.x)
+        march_channel(A, ch, smem, t, tmem_thread(tbase, t));
+      tmem_sync();  // every thread's TMEM loads have completed (waited)
+      if (t / 32 == 0) tmem_dealloc<kCols>(tbase);
+    } else {
+      for (int ch = blockIdx.x; ch < A.n_ch; ch += gridDim.x) march_channel(A, ch, smem, t);
+    }
   }
 
   static BPM_DEV void run_item(const MarchArgs& A, int ch0, unsigned char* smem) {
+    static_assert(!TMEM, "work-queue items read their tables from L2");
     if (ch0 < A.n_ch) march_channel(A, ch0, smem, threadIdx.x);
   }
 };

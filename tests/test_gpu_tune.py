@@ -33,13 +33,18 @@ def fields(w, **form):
     return out, got
 
 
-@pytest.mark.parametrize("nx,n_ch", [(1024, 611), (4096, 160)])
+@pytest.mark.parametrize("nx,n_ch", [(1024, 611), (2048, 310), (4096, 160), (8192, 40)])
 def test_every_2d_form_gives_identical_fields(nx, n_ch):
+    """Shared-memory (G = 1 and the maximum), L2, parked and parked-TMEM forms."""
     w = deformed_small(nx, nz=48, n_ch=n_ch, seed=31)
-    maxg = {1024: 4, 4096: 1}[nx]
+    maxg = {1024: 4, 2048: 2, 4096: 1, 8192: 1}[nx]
     ref, _ = fields(w, form=0, channels_per_block=1)
-    forms = [dict(form=0, channels_per_block=maxg), dict(form=1, channels_per_block=maxg),
-             dict(form=2, channels_per_block=1)]
+    forms = [dict(form=0, channels_per_block=maxg)]
+    if nx <= 4096:
+        forms.append(dict(form=1, channels_per_block=maxg))
+        forms.append(dict(form=2, channels_per_block=1))
+    if nx >= 2048:
+        forms.append(dict(form=3, channels_per_block=1))
     for f in forms:
         got, used = fields(w, **f)
         assert used["form"] == f["form"] and used["channels_per_block"] == f["channels_per_block"]

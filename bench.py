@@ -484,8 +484,10 @@ def main():
     # launch form chosen by the autotuner (untimed setup)
     # (256 steps: short runs over-weight the one-time per-channel table copy of
     # the shared-memory form)
-    _, tried = bpm.tune(w.dims, w.nx, w.ny, w.dx, w.dy, w.dz, w.n_ch,
-                        split_order=w.split_order, steps=min(w.nz, 256))
+    tried = []
+    if args.launch_form is None:
+        _, tried = bpm.tune(w.dims, w.nx, w.ny, w.dx, w.dy, w.dz, w.n_ch,
+                            split_order=w.split_order, steps=min(w.nz, 256))
     plan = bpm.Plan(w.dims, w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.n_ch, stream=stream,
                     zassenhaus=w.zassenhaus, split_order=w.split_order)
     plan.set_timing(True)

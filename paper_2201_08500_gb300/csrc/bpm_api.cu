@@ -1032,7 +1032,7 @@ struct RoundSlot {
   BatchItem* h_items = nullptr;
   MarchArgs* d_plans = nullptr;
   BatchItem* d_items = nullptr;
-  int* d_counter = nullptr;  // [4]: one counter per queue
+  int* d_counter = nullptr;  // [kQueueCount]: one counter per queue
   int cap_plans = 0, cap_items = 0;
   cudaEvent_t free_ev = nullptr;  // recorded after the round's kernels
   bool used = false;
@@ -1096,7 +1096,8 @@ cudaError_t slot_reserve(RoundSlot& r, int n_plans, int n_items) {
     if ((e = cudaMallocHost(&r.h_items, sizeof(BatchItem) * r.cap_items)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&r.d_items, sizeof(BatchItem) * r.cap_items)) != cudaSuccess) return e;
   }
-  if (!r.d_counter && (e = cudaMalloc(&r.d_counter, 4 * sizeof(int))) != cudaSuccess) return e;
+  if (!r.d_counter && (e = cudaMalloc(&r.d_counter, kQueueCount * sizeof(int))) != cudaSuccess)
+    return e;
   if (!r.free_ev && (e = cudaEventCreateWithFlags(&r.free_ev, cudaEventDisableTiming)) != cudaSuccess)
     return e;
   return cudaSuccess;
@@ -1141,7 +1142,7 @@ bpm_status enqueue_round(bpm_batch b, RoundSlot& r, int chunk) {
     if (!e.finishing && !e.cancelled && e.plan->z < e.plan->grid.nz) act.push_back(i);
   }
   if (act.empty()) return BPM_OK;
-  // four queues: (Nx = 8192 or not) x (Strang or first order), each sorted longest first
+  // queues by transform size and splitting order (BatchQueue), each sorted longest first
   struct Tmp {
     BatchItem it;
     double cost;
@@ -1153,8 +1154,8 @@ bpm_status enqueue_round(bpm_batch b, RoundSlot& r, int chunk) {
     bpm_plan p = b->entries[act[k]].plan;
     const int n = p->grid.nx;
     steps[k] = std::min(chunk, p->grid.nz - p->z);
-    const int G = batch_group(n);
-    const int q = (n == 8192 ? 0 : 2) + (p->grid.split_order == 2 ? 0 : 1);
+    const int G = batch_item_channels(n, p->grid.split_order);
+    const int q = batch_queue(n, p->grid.split_order);
     for (int c0 = 0; c0 < p->n_ch; c0 += G) {
       Tmp t;
       t.it = BatchItem{k, c0, n, 0};
@@ -1166,7 +1167,7 @@ bpm_status enqueue_round(bpm_batch b, RoundSlot& r, int chunk) {
   std::stable_sort(tmp.begin(), tmp.end(), [](const Tmp& x, const Tmp& y) {
     return x.q != y.q ? x.q < y.q : x.cost > y.cost;
   });
-  int cnt[4] = {0, 0, 0, 0};
+  int cnt[kQueueCount] = {};
   for (auto& t : tmp) cnt[t.q]++;
   BPM_BCUDA(b, slot_reserve(r, int(act.size()), int(tmp.size())), "batch staging");
   if (r.used) BPM_BCUDA(b, cudaEventSynchronize(r.free_ev), "staging reuse");
@@ -1178,18 +1179,21 @@ bpm_status enqueue_round(bpm_batch b, RoundSlot& r, int chunk) {
                                cudaMemcpyHostToDevice, b->stream), "upload round");
   BPM_BCUDA(b, cudaMemcpyAsync(r.d_items, r.h_items, sizeof(BatchItem) * tmp.size(),
                                cudaMemcpyHostToDevice, b->stream), "upload items");
-  BPM_BCUDA(b, cudaMemsetAsync(r.d_counter, 0, 4 * sizeof(int), b->stream), "clear queues");
-  // Queues run back to back, each on every SM: the Nx = 8192 items (the
-  // longest) first, then the smaller ones; the idle tail is one item per queue.
+  BPM_BCUDA(b, cudaMemsetAsync(r.d_counter, 0, kQueueCount * sizeof(int), b->stream),
+            "clear queues");
+  // Queues run back to back, each on every SM (or the batch's cap) with its
+  // blocks per SM: the Nx = 8192 items (the longest) first, then the smaller
+  // ones; the idle tail is one item per queue.
   int off = 0;
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < kQueueCount; ++q) {
     if (cnt[q] > 0)
-      BPM_BCUDA(b, launch_batch(r.d_plans, r.d_items + off, cnt[q], r.d_counter + q, q < 2,
-                                (q % 2) == 0, std::min(cnt[q], sms), b->stream),
+      BPM_BCUDA(b, launch_batch(r.d_plans, r.d_items + off, cnt[q], r.d_counter + q, q,
+                                std::min(cnt[q], sms * batch_blocks_per_sm(q)), b->stream),
                 "batch kernel");
     off += cnt[q];
   }
-  const int n_small = cnt[2] + cnt[3], n_big = cnt[0] + cnt[1];
+  const int n_big = cnt[kQueueTm8192] + cnt[kQueueBig2];
+  const int n_small = int(tmp.size()) - n_big;
   BPM_BCUDA(b, cudaEventRecord(r.free_ev, b->stream), "round event");
   r.used = true;
   b->last_items[0] = n_small;
@@ -1348,7 +1352,7 @@ BPM_API bpm_status bpm_batch_run_graph(bpm_batch b) {
     // allocations happen before the capture: staging for every item, completion events
     int n_items = 0;
     for (auto& e : b->entries) {
-      const int G = batch_group(e.plan->grid.nx);
+      const int G = batch_item_channels(e.plan->grid.nx, e.plan->grid.split_order);
       n_items += (e.plan->n_ch + G - 1) / G;
       if (!e.done) BPM_BCUDA(b, cudaEventCreateWithFlags(&e.done, cudaEventDisableTiming), "event");
     }

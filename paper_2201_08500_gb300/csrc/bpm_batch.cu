@@ -7,7 +7,8 @@
 // (T = Nx/16 threads per channel): Nx = 256, 512, 1024, 2048, 4096 pack 16, 8,
 // 4, 2, 1 channels into the 256-thread block, each with its own shared-memory
 // slot (at most 196 KB).  Nx = 8192 needs 512 threads and runs in a sibling
-// kernel of the same structure, with the parked-envelope body (bpm_parked.cuh).  The counter lives in global memory and is
+// kernel of the same structure, with the parked-envelope body (bpm_parked.cuh).
+// First-order items at Nx >= 2048 run in the tensor-memory kernels below.  The counter lives in global memory and is
 // cleared before each launch; the queue never waits, so no block can hang.
 #include <cuda_runtime.h>
 
@@ -73,32 +74,103 @@ __global__ void __launch_bounds__(512, 1)
   }
 }
 
+// First-order items at Nx = 2048, 4096, 8192 in the parked form with the
+// tables in tensor memory (Parked<N, 1, true>, the fastest single-plan form
+// there): one channel per item, N/16 threads per block, 512/(N/16) blocks per
+// SM; every block allocates its TMEM columns once and frees them on exit.
+template <int N>
+__global__ void __launch_bounds__(N / 16, 512 / (N / 16))
+    batch_kernel_tm(const MarchArgs* __restrict__ plans, const BatchItem* __restrict__ items,
+                    int n_items, int* counter) {
+  using P = Parked<N, 1, true>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_item;
+  __shared__ uint32_t s_tbase;
+  if (threadIdx.x / 32 == 0) tmem_alloc<P::kCols>(&s_tbase);
+  tmem_sync();
+  const uint32_t tcol = P::tmem_thread(s_tbase, threadIdx.x);
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= n_items) break;
+    const BatchItem item = items[it];
+    const MarchArgs& A = plans[item.plan];
+    if (item.ch0 < A.n_ch) P::march_channel(A, item.ch0, smem, threadIdx.x, tcol);
+  }
+  tmem_sync();
+  if (threadIdx.x / 32 == 0) tmem_dealloc<P::kCols>(s_tbase);
+}
+
 }  // namespace
 
 int batch_group(int n) { return n == 8192 ? 1 : kSmallThreads / (n / 16); }
 
+int batch_item_channels(int n, int split_order) {
+  return (split_order == 1 && n >= 2048) ? 1 : batch_group(n);
+}
+
+int batch_queue(int n, int split_order) {
+  if (split_order == 1) {
+    if (n == 8192) return kQueueTm8192;
+    if (n == 4096) return kQueueTm4096;
+    if (n == 2048) return kQueueTm2048;
+    return kQueueSmall;
+  }
+  return n == 8192 ? kQueueBig2 : kQueueSmall2;
+}
+
+int batch_blocks_per_sm(int queue) {
+  switch (queue) {
+    case kQueueTm4096: return 2;
+    case kQueueTm2048: return 4;
+    default: return 1;
+  }
+}
+
 cudaError_t launch_batch(const MarchArgs* plans, const BatchItem* items, int n_items, int* counter,
-                         bool big, bool strang, int blocks, cudaStream_t s) {
+                         int queue, int blocks, cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
   const size_t big_smem = Parked<8192, 1>::smem_bytes();
-  if (!big && !strang)
-    batch_kernel<false><<<blocks, kSmallThreads, kSmallSmem, s>>>(plans, items, n_items, counter);
-  else if (!big)
-    batch_kernel<true><<<blocks, kSmallThreads, kSmallSmem, s>>>(plans, items, n_items, counter);
-  else if (!strang)
-    batch_kernel_8192<false><<<blocks, 512, big_smem, s>>>(plans, items, n_items, counter);
-  else
-    batch_kernel_8192<true><<<blocks, 512, big_smem, s>>>(plans, items, n_items, counter);
+  switch (queue) {
+    case kQueueTm8192:
+      batch_kernel_tm<8192><<<blocks, 512, Parked<8192, 1, true>::smem_bytes(), s>>>(
+          plans, items, n_items, counter);
+      break;
+    case kQueueTm4096:
+      batch_kernel_tm<4096><<<blocks, 256, Parked<4096, 1, true>::smem_bytes(), s>>>(
+          plans, items, n_items, counter);
+      break;
+    case kQueueTm2048:
+      batch_kernel_tm<2048><<<blocks, 128, Parked<2048, 1, true>::smem_bytes(), s>>>(
+          plans, items, n_items, counter);
+      break;
+    case kQueueSmall:
+      batch_kernel<false><<<blocks, kSmallThreads, kSmallSmem, s>>>(plans, items, n_items, counter);
+      break;
+    case kQueueBig2:
+      batch_kernel_8192<true><<<blocks, 512, big_smem, s>>>(plans, items, n_items, counter);
+      break;
+    case kQueueSmall2:
+      batch_kernel<true><<<blocks, kSmallThreads, kSmallSmem, s>>>(plans, items, n_items, counter);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
 cudaError_t batch_set_attributes() {
   const int small = int(kSmallSmem), big = int(Parked<8192, 1>::smem_bytes());
+  const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t r[] = {
-      cudaFuncSetAttribute(batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, small),
-      cudaFuncSetAttribute(batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, small),
-      cudaFuncSetAttribute(batch_kernel_8192<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big),
-      cudaFuncSetAttribute(batch_kernel_8192<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)};
+      cudaFuncSetAttribute(batch_kernel<false>, attr, small),
+      cudaFuncSetAttribute(batch_kernel<true>, attr, small),
+      cudaFuncSetAttribute(batch_kernel_8192<true>, attr, big),
+      cudaFuncSetAttribute(batch_kernel_tm<8192>, attr, int(Parked<8192, 1, true>::smem_bytes())),
+      cudaFuncSetAttribute(batch_kernel_tm<4096>, attr, int(Parked<4096, 1, true>::smem_bytes())),
+      cudaFuncSetAttribute(batch_kernel_tm<2048>, attr, int(Parked<2048, 1, true>::smem_bytes()))};
   for (cudaError_t e : r)
     if (e != cudaSuccess) return e;
   return cudaSuccess;

@@ -76,10 +76,23 @@ struct BatchItem {
   int reserved;
 };
 
-// Work-queue launchers (bpm_batch.cu).  big selects the Nx = 8192 kernel.
-int batch_group(int n);
+// Work-queue launchers (bpm_batch.cu).  A round sorts its items into queues,
+// launched back to back in this order (longest items first within each):
+enum BatchQueue {
+  kQueueTm8192 = 0,  // first order, Nx = 8192: parked form, TMEM tables
+  kQueueBig2,        // Strang, Nx = 8192: parked form, L2 tables
+  kQueueTm4096,      // first order, Nx = 4096: parked form, TMEM tables, 2 blocks / SM
+  kQueueTm2048,      // first order, Nx = 2048: parked form, TMEM tables, 4 blocks / SM
+  kQueueSmall,       // first order, Nx <= 1024: resident form, G channels per block
+  kQueueSmall2,      // Strang, Nx <= 4096: resident form
+  kQueueCount
+};
+int batch_group(int n);                               // channels per block of the resident kernels
+int batch_item_channels(int n, int split_order);      // channels per item
+int batch_queue(int n, int split_order);
+int batch_blocks_per_sm(int queue);
 cudaError_t launch_batch(const MarchArgs* plans, const BatchItem* items, int n_items, int* counter,
-                         bool big, bool strang, int blocks, cudaStream_t s);
+                         int queue, int blocks, cudaStream_t s);
 
 // Host runtime helpers (bpm_api.cu): FFT constants of size n (twiddles, spectrum
 // order, round-trip gain; host memory owned by a process-wide cache) and a

@@ -35,11 +35,15 @@ from paper_2201_08500_gb300 import workloads  # noqa: E402
 
 METRIC = "BPM cell-updates/s (omega*x*z)"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
-# default march, from one ncu capture of that launch (597.55 MB read, 62.88 MB
-# written): the per-launch deformation rows are re-read by each of the ~7
-# waves of channels, which at 9.7 GB/s is immaterial to this ALU-bound kernel.
-# Keyed by kernel and workload; any other configuration reports null.
-MEASURED_TRAFFIC = {("march_kernel<4096,1>", "deformed-2d-nx4096-nz2000-ch1024", 1): 660.43e6}
+# default march, from one ncu capture of that launch per launch form: form 0
+# 597.55 MB read + 62.88 MB written, form 3 545.52 + 55.38 MB.  The deformation
+# rows are re-read by each wave of channels, which at ~9 GB/s is immaterial to
+# this ALU-bound kernel.  Keyed by kernel, form and workload; any other
+# configuration reports null.
+MEASURED_TRAFFIC = {
+    ("march_kernel<4096,1> form 0", "deformed-2d-nx4096-nz2000-ch1024", 1): 660.43e6,
+    ("march_kernel<4096,1> form 3", "deformed-2d-nx4096-nz2000-ch1024", 1): 600.90e6,
+}
 UNIT = "cell-updates/s"
 FP32_LANES_PER_SM = 128
 
@@ -556,6 +560,8 @@ def main():
     # in and out (32 B), one read of the deformation rows (8 B per x and step)
     sets = 2 if w.split_order == 4 else 1
     alg_bytes = w.n_ch * n * (32 * sets + 32) + w.nz * n * 8
+    form = plan.launch()["form"]
+    kernel = f"march_kernel<{n},{st['channels_per_block']}> form {form}"
     props = torch.cuda.get_device_properties(local)
     pk = measured_peaks()
     sm_max = pk.get("sm_max_mhz", 2070.0)
@@ -575,11 +581,9 @@ def main():
                        "launch": plan.launch(), "tuned": tried},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak,
-                         "traffic": MEASURED_TRAFFIC.get(
-                             (f"march_kernel<{n},{st['channels_per_block']}>", w.name,
-                              w.split_order)),
+                         "traffic": MEASURED_TRAFFIC.get((kernel, w.name, w.split_order)),
                          "algorithmic_bytes": alg_bytes,
-                         "kernel": f"march_kernel<{n},{st['channels_per_block']}>",
+                         "kernel": kernel,
                          "flops_per_cell_update": flops_per_cell(n, w.split_order),
                          "march_ms": march_avg,
                          "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 "

@@ -151,6 +151,26 @@ std::vector<float2> twiddle_order(int n) {
   return out;
 }
 
+// The same twiddles in pairs for 128-bit loads: stage s, outputs m = 2i+1 and
+// 2i+2 (i = 0..7; the second half of pair 7 is padding) of thread index j < ln
+// at float2 offset 2 (off(s) + i ln + j), off(s) = sum over earlier stages of
+// 8 ln.  Same FP32 values as twiddle_order.
+std::vector<float2> twiddle_pairs(int n) {
+  const FftConsts& f = fft_consts(n);
+  const int logn = ilog2i(n);
+  const int S = (logn + 3) / 4;
+  std::vector<float2> out;
+  for (int s = 0; s < S - 1; ++s) {
+    const int ls = n >> (4 * s), ln = n >> (4 * (s + 1)), stride = n / ls;
+    for (int i = 0; i < 8; ++i)
+      for (int j = 0; j < ln; ++j) {
+        out.push_back(f.tw[(size_t(stride) * j * (2 * i + 1)) % n]);
+        out.push_back(i < 7 ? f.tw[(size_t(stride) * j * (2 * i + 2)) % n] : make_float2(0.f, 0.f));
+      }
+  }
+  return out;
+}
+
 struct DeviceInfo {
   int sm_count = 0;
   int cc = 0;
@@ -217,6 +237,7 @@ struct bpm_plan_s {
   ChannelCoef* coef = nullptr;
   float2* twiddle = nullptr;
   float2* twiddle_t = nullptr;   // 2D: stage twiddles in thread order
+  float2* twiddle_p = nullptr;   // 2D: the same in thread-ordered pairs
   int* rev = nullptr;
   double* gain = nullptr;
   double* omega = nullptr;
@@ -278,7 +299,7 @@ void free_plan_buffers(bpm_plan p) {
   void* ptrs[] = {p->cfield, p->e0,      p->eh,    p->tables, p->coef,     p->twiddle,
                   p->rev,    p->gain,    p->omega, p->weight, p->inc_norm, p->refl,
                   p->trans,  p->eh_time, p->dflag, p->u_tmp,  p->gcorr,    p->twy,
-                  p->qy,     p->spec,    p->twx3,  p->twiddle_t};
+                  p->qy,     p->spec,    p->twx3,  p->twiddle_t, p->twiddle_p};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->ev0) cudaEventDestroy(p->ev0);
@@ -336,7 +357,7 @@ size_t plan_bytes(const bpm_grid& g, int n_ch) {
          2 * nf * sizeof(float2);
   b += sets * n_ch * sizeof(ChannelCoef);
   b += size_t(g.nx) * (sizeof(float2) + sizeof(int) + sizeof(double));
-  if (g.dims == 2) b += size_t(g.nx) * sizeof(float2);  // thread-order twiddles
+  if (g.dims == 2) b += 3 * size_t(g.nx) * sizeof(float2);  // thread-order twiddles, pairs
   b += size_t(n_ch) * (5 * sizeof(double) + sizeof(double2));
   b += nf * sizeof(double2);                       // time response
   return b;
@@ -421,6 +442,7 @@ BPM_API bpm_status bpm_plan_create(const bpm_grid* grid, int n_channels, void* c
   check(dalloc(&p->coef, sets * n_channels), "alloc coefficients");
   check(dalloc(&p->twiddle, size_t(g.nx)), "alloc twiddles");
   if (g.dims == 2) check(dalloc(&p->twiddle_t, size_t(g.nx)), "alloc thread-order twiddles");
+  if (g.dims == 2) check(dalloc(&p->twiddle_p, 2 * size_t(g.nx)), "alloc paired twiddles");
   check(dalloc(&p->rev, size_t(g.nx)), "alloc spectrum order");
   check(dalloc(&p->gain, size_t(g.nx)), "alloc gain");
   check(dalloc(&p->omega, size_t(n_channels)), "alloc omega");
@@ -447,12 +469,16 @@ BPM_API bpm_status bpm_plan_create(const bpm_grid* grid, int n_channels, void* c
   check(cudaMemcpyAsync(p->twiddle, fc.tw.data(), sizeof(float2) * g.nx, cudaMemcpyHostToDevice,
                         p->stream),
         "upload twiddles");
-  std::vector<float2> tw_ord;
+  std::vector<float2> tw_ord, tw_pair;
   if (g.dims == 2) {
     tw_ord = twiddle_order(g.nx);
     check(cudaMemcpyAsync(p->twiddle_t, tw_ord.data(), sizeof(float2) * tw_ord.size(),
                           cudaMemcpyHostToDevice, p->stream),
           "upload thread-order twiddles");
+    tw_pair = twiddle_pairs(g.nx);
+    check(cudaMemcpyAsync(p->twiddle_p, tw_pair.data(), sizeof(float2) * tw_pair.size(),
+                          cudaMemcpyHostToDevice, p->stream),
+          "upload paired twiddles");
   }
   check(cudaMemcpyAsync(p->rev, fc.rev.data(), sizeof(int) * g.nx, cudaMemcpyHostToDevice,
                         p->stream),
@@ -654,6 +680,7 @@ BPM_API bpm_status bpm_run(bpm_plan p, int n_steps) {
   a.coef = p->coef;
   a.twiddle = p->twiddle;
   a.twiddle_t = p->twiddle_t;
+  a.twiddle_p = p->twiddle_p;
   a.cfield = p->cfield;
   a.e0 = p->e0;
   a.eh = p->eh;
@@ -1119,6 +1146,7 @@ MarchArgs march_args(bpm_plan p, int n_steps) {
   a.coef = p->coef;
   a.twiddle = p->twiddle;
   a.twiddle_t = p->twiddle_t;
+  a.twiddle_p = p->twiddle_p;
   a.cfield = p->cfield;
   a.e0 = p->e0;
   a.eh = p->eh;

@@ -82,7 +82,7 @@ template <int N>
 __global__ void __launch_bounds__(N / 16, 512 / (N / 16))
     batch_kernel_tm(const MarchArgs* __restrict__ plans, const BatchItem* __restrict__ items,
                     int n_items, int* counter) {
-  using P = Parked<N, 1, true>;
+  using P = Parked<N, 1, true, false>;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
   __shared__ uint32_t s_tbase;
@@ -135,15 +135,15 @@ cudaError_t launch_batch(const MarchArgs* plans, const BatchItem* items, int n_i
   const size_t big_smem = Parked<8192, 1>::smem_bytes();
   switch (queue) {
     case kQueueTm8192:
-      batch_kernel_tm<8192><<<blocks, 512, Parked<8192, 1, true>::smem_bytes(), s>>>(
+      batch_kernel_tm<8192><<<blocks, 512, Parked<8192, 1, true, false>::smem_bytes(), s>>>(
           plans, items, n_items, counter);
       break;
     case kQueueTm4096:
-      batch_kernel_tm<4096><<<blocks, 256, Parked<4096, 1, true>::smem_bytes(), s>>>(
+      batch_kernel_tm<4096><<<blocks, 256, Parked<4096, 1, true, false>::smem_bytes(), s>>>(
           plans, items, n_items, counter);
       break;
     case kQueueTm2048:
-      batch_kernel_tm<2048><<<blocks, 128, Parked<2048, 1, true>::smem_bytes(), s>>>(
+      batch_kernel_tm<2048><<<blocks, 128, Parked<2048, 1, true, false>::smem_bytes(), s>>>(
           plans, items, n_items, counter);
       break;
     case kQueueSmall:
@@ -168,9 +168,9 @@ cudaError_t batch_set_attributes() {
       cudaFuncSetAttribute(batch_kernel<false>, attr, small),
       cudaFuncSetAttribute(batch_kernel<true>, attr, small),
       cudaFuncSetAttribute(batch_kernel_8192<true>, attr, big),
-      cudaFuncSetAttribute(batch_kernel_tm<8192>, attr, int(Parked<8192, 1, true>::smem_bytes())),
-      cudaFuncSetAttribute(batch_kernel_tm<4096>, attr, int(Parked<4096, 1, true>::smem_bytes())),
-      cudaFuncSetAttribute(batch_kernel_tm<2048>, attr, int(Parked<2048, 1, true>::smem_bytes()))};
+      cudaFuncSetAttribute(batch_kernel_tm<8192>, attr, int(Parked<8192, 1, true, false>::smem_bytes())),
+      cudaFuncSetAttribute(batch_kernel_tm<4096>, attr, int(Parked<4096, 1, true, false>::smem_bytes())),
+      cudaFuncSetAttribute(batch_kernel_tm<2048>, attr, int(Parked<2048, 1, true, false>::smem_bytes()))};
   for (cudaError_t e : r)
     if (e != cudaSuccess) return e;
   return cudaSuccess;

@@ -25,6 +25,7 @@ struct MarchArgs {
   const ChannelCoef* coef;   // [n_ch]
   const float2* twiddle;     // [N] exp(-2 pi i k / N), FP32 correctly rounded
   const float2* twiddle_t;   // stage twiddles in thread order (kernels that read them from memory)
+  const float2* twiddle_p;   // the same in thread-ordered pairs (parked forms, 128-bit loads)
   const float2* cfield;      // [nz][N] Pi(x, z) exp(+i h u(x, z)); 0 outside the crystal
   float2* e0;                // [n_ch][N]
   float2* eh;                // [n_ch][N]

@@ -34,7 +34,7 @@ namespace bpm {
 // TMEM = true keeps each thread's propagator-table slice in tensor memory
 // (bpm_tmem.cuh, 128 columns per thread: 2 envelopes x 16 positions x hi/lo
 // float4) instead of reading it from L2 every step (one table set: SPLIT 1, 2).
-template <int N, int SPLIT = 1, bool TMEM = false>
+template <int N, int SPLIT = 1, bool TMEM = false, bool WIDE = (N <= 4096)>
 struct Parked {
   static_assert(SPLIT == 1 || SPLIT == 2 || SPLIT == 4, "splitting order");
   static_assert(!TMEM || SPLIT != 4, "TMEM tables: one table set");
@@ -45,6 +45,11 @@ struct Parked {
   // TMEM columns of the block: warps w and w + 4 share lanes, so each group of
   // four warps takes its own 128 columns
   static constexpr int kCols = 128 * (T >= 128 ? T / 128 : 1);
+  // Wide layout (default at N <= 4096): stage twiddles loaded in 128-bit pairs
+  // and the parked envelope in 128-bit slots.  At N = 8192 (128 registers for a
+  // 512-thread block) and in the work-queue kernels the narrower per-element
+  // layout spills less and measured faster.
+  static constexpr bool kWide = WIDE;
 
   __host__ __device__ static constexpr size_t xbuf_bytes() { return size_t(Pad<N>::kSlots) * sizeof(float2); }
   __host__ __device__ static constexpr size_t vec_bytes() { return size_t(N) * sizeof(float2); }
@@ -53,7 +58,8 @@ struct Parked {
     return xbuf_bytes() + 2 * vec_bytes() + red_bytes();
   }
 
-  // Offset of stage s in the thread-ordered twiddle table (see twiddle_order).
+  // Per-element stage twiddles (twiddle_order on the host): stage s, output m
+  // of thread t at tw_off(s) + (m - 1) LN(s) + t % LN(s).
   __host__ __device__ static constexpr int tw_off(int s) {
     return s == 0 ? 0 : tw_off(s - 1) + 15 * Gm::LN(s - 1);
   }
@@ -63,22 +69,54 @@ struct Parked {
     return __ldg(tw + tw_off(s) + (m - 1) * ln + (t % ln));
   }
 
+  // Stage twiddles in pairs (see twiddle_pairs on the host): stage s, outputs
+  // m = 2i+1, 2i+2 (i = 0..7, the last pair padded) of thread t at float4
+  // pair_off(s) + i LN(s) + t % LN(s), so one 128-bit load serves two outputs.
+  __host__ __device__ static constexpr int pair_off(int s) {
+    return s == 0 ? 0 : pair_off(s - 1) + 8 * Gm::LN(s - 1);
+  }
   template <int s>
-  static BPM_DEV void stage_fwd(float2 (&v)[16], const float2* tw, int t) {
+  static BPM_DEV float4 twiddle_pair(const float4* tw, int t, int i) {
+    constexpr int ln = Gm::LN(s);
+    return __ldg(tw + pair_off(s) + i * ln + (t % ln));
+  }
+
+  template <int s>
+  static BPM_DEV void stage_fwd(float2 (&v)[16], const float4* tw, int t) {
     if constexpr (s < S - 1) {
       dft16_fwd(v);
+      if constexpr (kWide) {
 #pragma unroll
-      for (int m = 1; m < 16; ++m) v[m] = c_mul(v[m], twiddle<s>(tw, t, m));
+        for (int i = 0; i < 8; ++i) {
+          const float4 w = twiddle_pair<s>(tw, t, i);
+          v[2 * i + 1] = c_mul(v[2 * i + 1], make_float2(w.x, w.y));
+          if (i < 7) v[2 * i + 2] = c_mul(v[2 * i + 2], make_float2(w.z, w.w));
+        }
+      } else {
+        const float2* t1 = reinterpret_cast<const float2*>(tw);
+#pragma unroll
+        for (int m = 1; m < 16; ++m) v[m] = c_mul(v[m], twiddle<s>(t1, t, m));
+      }
     } else {
       last_stage<Gm::RLAST, false>(v);
     }
   }
 
   template <int s>
-  static BPM_DEV void stage_inv(float2 (&v)[16], const float2* tw, int t) {
+  static BPM_DEV void stage_inv(float2 (&v)[16], const float4* tw, int t) {
     if constexpr (s < S - 1) {
+      if constexpr (kWide) {
 #pragma unroll
-      for (int m = 1; m < 16; ++m) v[m] = c_mulc(v[m], twiddle<s>(tw, t, m));
+        for (int i = 0; i < 8; ++i) {
+          const float4 w = twiddle_pair<s>(tw, t, i);
+          v[2 * i + 1] = c_mulc(v[2 * i + 1], make_float2(w.x, w.y));
+          if (i < 7) v[2 * i + 2] = c_mulc(v[2 * i + 2], make_float2(w.z, w.w));
+        }
+      } else {
+        const float2* t1 = reinterpret_cast<const float2*>(tw);
+#pragma unroll
+        for (int m = 1; m < 16; ++m) v[m] = c_mulc(v[m], twiddle<s>(t1, t, m));
+      }
       dft16_inv(v);
     } else {
       last_stage<Gm::RLAST, true>(v);
@@ -120,7 +158,7 @@ struct Parked {
   }
 
   static BPM_DEV void propagate(float2 (&v)[16], float2* x, const float4* gt, uint32_t tcol,
-                                const float2* tw, int t) {
+                                const float4* tw, int t) {
     static_assert(S == 3 || S == 4, "parked form: 1024 <= N <= 8192");
     stage_fwd<0>(v, tw, t);
     exchange<0, 1>(v, x, t);
@@ -143,41 +181,111 @@ struct Parked {
     stage_inv<0>(v, tw, t);
   }
 
+  // Parking, thread-private.  Wide: the 16 values as 8 float4 pairs
+  // (v[2i], v[2i+1]) at slot 8 t + ((i + t) & 7), free of bank conflicts for
+  // the 8 threads of a 128-bit phase.  Narrow: value k at k T + t (64-bit).
+  static BPM_DEV int park_slot(int t, int i) { return 8 * t + ((i + t) & 7); }
+  static BPM_DEV void park(const float2 (&v)[16], float2* p, int t) {
+    if constexpr (kWide) {
+      float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        q[park_slot(t, i)] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) p[k * T + t] = v[k];
+    }
+  }
+  static BPM_DEV void unpark(float2 (&v)[16], const float2* p, int t) {
+    if constexpr (kWide) {
+      const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float4 w = q[park_slot(t, i)];
+        v[2 * i] = make_float2(w.x, w.y);
+        v[2 * i + 1] = make_float2(w.z, w.w);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) v[k] = p[k * T + t];
+    }
+  }
+  // Parked value k of this thread.
+  static BPM_DEV float2 parked(const float2* p, int t, int k) {
+    if constexpr (kWide) {
+      const float4 w = reinterpret_cast<const float4*>(p)[park_slot(t, k / 2)];
+      return (k % 2 == 0) ? make_float2(w.x, w.y) : make_float2(w.z, w.w);
+    } else {
+      return p[k * T + t];
+    }
+  }
+
   // [E0 in v, Eh parked] -> [Eh in v, E0 parked], both propagated (table set gt).
   static BPM_DEV void propagate_both(float2 (&v)[16], float2* x, float2* p0, float2* ph,
-                                     const float4* gt, uint32_t tcol, const float2* tw, int t) {
+                                     const float4* gt, uint32_t tcol, const float4* tw, int t) {
     propagate(v, x, gt, tcol, tw, t);
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      p0[k * T + t] = v[k];
-      v[k] = ph[k * T + t];
-    }
+    park(v, p0, t);
+    unpark(v, ph, t);
     propagate(v, x, gt + N, tcol + 64u, tw, t);
   }
 
   // [Eh in v, E0 parked] -> coupling at z_n -> [E0 in v, Eh parked].
   static BPM_DEV void couple_back(float2 (&v)[16], const float2* p0, float2* ph,
                                   const float2* crow, const ChannelCoef& cf, int t) {
+    if constexpr (kWide) {
+      const float4* q0 = reinterpret_cast<const float4*>(p0);
+      float4* qh = reinterpret_cast<float4*>(ph);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const float2 c = __ldg(crow + t + T * k);
-      float2 e0 = p0[k * T + t], eh = v[k];
-      if (c.x != 0.f || c.y != 0.f) couple_cell(e0, eh, c, cf);
-      ph[k * T + t] = eh;
-      v[k] = e0;
+      for (int i = 0; i < 8; ++i) {  // pair (2i, 2i+1)
+        const float4 w = q0[park_slot(t, i)];
+        float2 e0[2] = {make_float2(w.x, w.y), make_float2(w.z, w.w)};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float2 c = __ldg(crow + t + T * (2 * i + h));
+          if (c.x != 0.f || c.y != 0.f) couple_cell(e0[h], v[2 * i + h], c, cf);
+        }
+        qh[park_slot(t, i)] =
+            make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
+        v[2 * i] = e0[0];
+        v[2 * i + 1] = e0[1];
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const float2 c = __ldg(crow + t + T * k);
+        float2 e0 = p0[k * T + t], eh = v[k];
+        if (c.x != 0.f || c.y != 0.f) couple_cell(e0, eh, c, cf);
+        ph[k * T + t] = eh;
+        v[k] = e0;
+      }
     }
   }
 
   // [E0 in v, Eh parked] -> coupling at z_n, same state.
   static BPM_DEV void couple_front(float2 (&v)[16], float2* ph, const float2* crow,
                                    const ChannelCoef& cf, int t) {
+    if constexpr (kWide) {
+      float4* qh = reinterpret_cast<float4*>(ph);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const float2 c = __ldg(crow + t + T * k);
-      if (c.x != 0.f || c.y != 0.f) {
-        float2 eh = ph[k * T + t];
-        couple_cell(v[k], eh, c, cf);
-        ph[k * T + t] = eh;
+      for (int i = 0; i < 8; ++i) {  // pair (2i, 2i+1)
+        const float4 w = qh[park_slot(t, i)];
+        float2 eh[2] = {make_float2(w.x, w.y), make_float2(w.z, w.w)};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float2 c = __ldg(crow + t + T * (2 * i + h));
+          if (c.x != 0.f || c.y != 0.f) couple_cell(v[2 * i + h], eh[h], c, cf);
+        }
+        qh[park_slot(t, i)] = make_float4(eh[0].x, eh[0].y, eh[1].x, eh[1].y);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const float2 c = __ldg(crow + t + T * k);
+        if (c.x != 0.f || c.y != 0.f) {
+          float2 eh = ph[k * T + t];
+          couple_cell(v[k], eh, c, cf);
+          ph[k * T + t] = eh;
+        }
       }
     }
   }
@@ -212,16 +320,16 @@ struct Parked {
     double* red = reinterpret_cast<double*>(ph + N);
     const float4* gtab = A.tables + size_t(ch) * kTabs * 2 * N;
     const ChannelCoef cf = A.coef[size_t(ch) * kTabs];
-    const float2* tw = A.twiddle_t;
+    const float4* tw = reinterpret_cast<const float4*>(kWide ? A.twiddle_p : A.twiddle_t);
     float2* e0 = A.e0 + size_t(ch) * N;
     float2* eh = A.eh + size_t(ch) * N;
     if constexpr (TMEM) tmem_fill(gtab, tcol, t);
     float2 v[16];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      v[k] = e0[t + T * k];
-      ph[k * T + t] = eh[t + T * k];
-    }
+    for (int k = 0; k < 16; ++k) v[k] = eh[t + T * k];
+    park(v, ph, t);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = e0[t + T * k];
     for (int step = 0; step < A.n_steps; ++step) {
       const float2* crow = A.cfield + size_t(A.z0 + step) * N;
       if constexpr (SPLIT == 4) {
@@ -241,7 +349,7 @@ struct Parked {
     double sa = 0.0, sb = 0.0;
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
-      const float2 m = ph[k * T + t];
+      const float2 m = parked(ph, t, k);
       e0[t + T * k] = v[k];
       eh[t + T * k] = m;
       sa += double(v[k].x) * v[k].x + double(v[k].y) * v[k].y;

@@ -201,6 +201,7 @@ BPM_API bpm_status bpm_run_noalloc(const bpm_grid* grid, int n_channels,
   a.coef = coef;
   a.twiddle = twiddle;
   a.twiddle_t = nullptr;  // nx <= 4096: twiddles stay in registers
+  a.twiddle_p = nullptr;
   a.cfield = cfield;
   a.e0 = e0;
   a.eh = eh;

@@ -196,8 +196,8 @@ BPM_API bpm_status bpm_get_stats(bpm_plan plan, bpm_stats* out);
  *                      per block and 512/(Nx/16) blocks per SM (first order,
  *                      Nx = 1024, 2048, 4096, channels_per_block = 1);
  *                      3 = parked with the tables in tensor memory (TMEM)
- *                      instead of L2 (first order, Nx = 2048, 4096, 8192,
- *                      channels_per_block = 1).
+ *                      instead of L2 (first order or Strang, Nx = 2048, 4096,
+ *                      8192, channels_per_block = 1).
  *   channels_per_block 2D march: 1, or the maximum of the size (16, 8, 4, 2, 1
  *                      for Nx = 256, 512, 1024, 2048, >= 4096).
  *   row_threads        3D row pass: 256 or 512 threads per block, i.e. a tile

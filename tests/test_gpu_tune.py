@@ -54,6 +54,18 @@ def test_every_2d_form_gives_identical_fields(nx, n_ch):
     assert e["per_ch"] < 1e-4, e
 
 
+@pytest.mark.parametrize("nx", [2048, 4096])
+def test_strang_tmem_form_gives_identical_fields(nx):
+    """Strang splitting in the tensor-memory parked form equals the resident form."""
+    w = deformed_small(nx, nz=40, n_ch=6, seed=32)
+    w.split_order = 2
+    ref, _ = fields(w, form=0, channels_per_block=1)
+    got, used = fields(w, form=3, channels_per_block=1)
+    assert used["form"] == 3
+    for k in ("e0", "eh", "R"):
+        assert np.array_equal(got[k], ref[k]), k
+
+
 def test_3d_row_tiles_give_identical_fields():
     from test_gpu_3d import case3d
     w = case3d(512, 256, 16, 2, seed=5)
@@ -77,6 +89,8 @@ def test_forms_a_plan_cannot_run_are_refused():
         q.set_launch(form=1, channels_per_block=16)  # the L2 form is first order only
     with pytest.raises(bpm.BpmError):
         q.set_launch(form=2, channels_per_block=1)   # so is the parked form (and Nx >= 1024)
+    with pytest.raises(bpm.BpmError):
+        q.set_launch(form=3, channels_per_block=1)   # the TMEM form needs Nx >= 2048
     q.close()
 
 

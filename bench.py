@@ -286,10 +286,15 @@ def run_3d(args, world, rank, local):
     u_dev = torch.from_numpy(np.ascontiguousarray(w.u)).cuda()
     w.u = None
     stream = torch.cuda.current_stream()
-    # launch form chosen by the autotuner (untimed setup): row-pass tile height
-    tuned, tried = bpm.tune(w.dims, w.nx, w.ny, w.dx, w.dy, w.dz, w.n_ch, steps=32)
+    # launch form chosen by the autotuner (untimed setup): column-pass form and
+    # row-pass tile height
+    tried = []
+    if args.launch_form is None:
+        _, tried = bpm.tune(w.dims, w.nx, w.ny, w.dx, w.dy, w.dz, w.n_ch, steps=32)
     plan = bpm.Plan(w.dims, w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.n_ch, stream=stream)
     plan.set_timing(True)
+    if args.launch_form is not None:
+        plan.set_launch(form=args.launch_form)
 
     def step():
         plan.set_crystal(w.chi0, w.chih, w.chihb, w.theta_B, w.lambda_B, w.x_surface,

@@ -139,6 +139,28 @@ struct Parked {
 
   // One envelope: forward FFT, digit-reversed spectrum times the tilted
   // propagator (hi + lo table gt of this envelope), inverse FFT.
+  // At N = 8192 (stages 16 x 16 x 16 x 2) the 32 positions of block b = t/2
+  // of the last two stages belong to the lane pair (2b, 2b+1) in both layouts
+  // (stage 2: 32 b + t%2 + 2k; stage 3: 16 t + k), so that exchange is done
+  // with register shuffles between the pair: no shared memory, no barrier.
+  static constexpr bool kPairLast = (S == 4 && Gm::RLAST == 2);
+
+  static BPM_DEV float2 shfl_pair(float2 v) {
+    return make_float2(__shfl_xor_sync(0xFFFFFFFFu, v.x, 1), __shfl_xor_sync(0xFFFFFFFFu, v.y, 1));
+  }
+  // In-place swap within the lane pair: the even lane sends v[8+i] and receives
+  // the odd lane's v[i] into it, the odd lane the reverse.  Applied to stage-2
+  // values it leaves the stage-3 positions 16 t + 2i in v[i] and 16 t + 2i + 1
+  // in v[8+i] of every lane; applied to that arrangement it restores stage 2.
+  static BPM_DEV void pair_swap(float2 (&v)[16], int t) {
+    const bool odd = t & 1;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float2 r = shfl_pair(odd ? v[i] : v[8 + i]);
+      if (odd) v[i] = r; else v[8 + i] = r;
+    }
+  }
+
   // Table multiply of one envelope: 16 positions, hi/lo float4 each, from L2
   // (gt) or from this thread's TMEM columns (tcol).
   static BPM_DEV void multiply(float2 (&v)[16], const float4* gt, uint32_t tcol, int t) {
@@ -165,14 +187,33 @@ struct Parked {
     stage_fwd<1>(v, tw, t);
     exchange<1, 2>(v, x, t);
     stage_fwd<2>(v, tw, t);
-    if constexpr (S == 4) {
-      exchange<2, 3>(v, x, t);
-      stage_fwd<3>(v, tw, t);
-    }
-    multiply(v, gt, tcol, t);
-    if constexpr (S == 4) {
-      stage_inv<3>(v, tw, t);
-      exchange<3, 2>(v, x, t);
+    if constexpr (kPairLast) {
+      pair_swap(v, t);
+      float2 w[16];  // stage-3 register order (a renaming, no data movement)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        w[2 * i] = v[i];
+        w[2 * i + 1] = v[8 + i];
+      }
+      stage_fwd<3>(w, tw, t);
+      multiply(w, gt, tcol, t);
+      stage_inv<3>(w, tw, t);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        v[i] = w[2 * i];
+        v[8 + i] = w[2 * i + 1];
+      }
+      pair_swap(v, t);
+    } else {
+      if constexpr (S == 4) {
+        exchange<2, 3>(v, x, t);
+        stage_fwd<3>(v, tw, t);
+      }
+      multiply(v, gt, tcol, t);
+      if constexpr (S == 4) {
+        stage_inv<3>(v, tw, t);
+        exchange<3, 2>(v, x, t);
+      }
     }
     stage_inv<2>(v, tw, t);
     exchange<2, 1>(v, x, t);

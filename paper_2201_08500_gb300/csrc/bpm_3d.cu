@@ -47,6 +47,19 @@ BPM_DEV void g3_sync(int g) {
   }
 }
 
+// Row-pass tile of R rows: element (c, r) (transposed-spectrum column c, tile
+// row r) of an envelope at c R + (r ^ tile_swz<R>(c)).  The XOR spreads every
+// 16-thread phase of the pass's 64-bit accesses over distinct banks: the
+// column-segment staging, the row reads and writes, and the FFT exchanges.
+template <int R>
+__host__ __device__ constexpr int tile_swz(int c) {
+  return R <= 16 ? (c / (16 / R)) % R : c % 16;
+}
+template <int R>
+BPM_DEV int tile_at(int c, int r) {
+  return c * R + (r ^ tile_swz<R>(c));
+}
+
 // Paired (E0, Eh) transform of size N held by a group of T = N/16 threads, 16
 // values per thread and envelope.  `buf` is the group's exchange area: element p
 // of envelope e lives at buf[(swz(p) * stride) + e * estride].
@@ -73,20 +86,31 @@ struct Fft2Env {
     }
   }
 
-  template <int SF, int ST>
+  // Slot of position p: TR = 0, swz(p) * stride; TR > 0, the row-pass tile of
+  // TR rows with this group's row g (buf is then the tile base).
+  template <int TR>
+  static BPM_DEV int slot(int p, int stride, int g) {
+    if constexpr (TR > 0) {
+      return tile_at<TR>(swz(p), g);
+    } else {
+      return swz(p) * stride;
+    }
+  }
+
+  template <int SF, int ST, int TR>
   static BPM_DEV void xchg(float2 (&a)[16], float2 (&b)[16], float2* buf, int stride, int estride,
                            int t, int g) {
     g3_sync<T>(g);
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
-      const int p = swz(Gm::template pos<SF>(t, k)) * stride;
+      const int p = slot<TR>(Gm::template pos<SF>(t, k), stride, g);
       buf[p] = a[k];
       buf[p + estride] = b[k];
     }
     g3_sync<T>(g);
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
-      const int p = swz(Gm::template pos<ST>(t, k)) * stride;
+      const int p = slot<TR>(Gm::template pos<ST>(t, k), stride, g);
       a[k] = buf[p];
       b[k] = buf[p + estride];
     }
@@ -116,30 +140,33 @@ struct Fft2Env {
     }
   }
 
-  // natural layout (pos<0>) -> digit-reversed spectrum (pos<S-1>)
+  // natural layout (pos<0>) -> digit-reversed spectrum (pos<S-1>).  TR > 0:
+  // exchanges through the row-pass tile of TR rows (see slot).
+  template <int TR = 0>
   static BPM_DEV void fwd(float2 (&a)[16], float2 (&b)[16], float2* buf, int stride, int estride,
                           const float2* tw, int t, int g) {
     sfwd<0>(a, b, tw, t);
     if constexpr (S > 1) {
-      xchg<0, 1>(a, b, buf, stride, estride, t, g);
+      xchg<0, 1, TR>(a, b, buf, stride, estride, t, g);
       sfwd<1>(a, b, tw, t);
     }
     if constexpr (S > 2) {
-      xchg<1, 2>(a, b, buf, stride, estride, t, g);
+      xchg<1, 2, TR>(a, b, buf, stride, estride, t, g);
       sfwd<2>(a, b, tw, t);
     }
     static_assert(S <= 3, "3D transforms up to 4096 points");
   }
 
+  template <int TR = 0>
   static BPM_DEV void inv(float2 (&a)[16], float2 (&b)[16], float2* buf, int stride, int estride,
                           const float2* tw, int t, int g) {
     if constexpr (S > 2) {
       sinv<2>(a, b, tw, t);
-      xchg<2, 1>(a, b, buf, stride, estride, t, g);
+      xchg<2, 1, TR>(a, b, buf, stride, estride, t, g);
     }
     if constexpr (S > 1) {
       sinv<1>(a, b, tw, t);
-      xchg<1, 0>(a, b, buf, stride, estride, t, g);
+      xchg<1, 0, TR>(a, b, buf, stride, estride, t, g);
     }
     sinv<0>(a, b, tw, t);
   }
@@ -158,20 +185,18 @@ __global__ void __launch_bounds__(RT, 512 / RT) row_pass_kernel(Pass3DArgs A) {
   constexpr int kRowThreads = RT;
   constexpr int T = NX / 16;
   constexpr int R = kRowThreads / T;  // rows per block
-  constexpr int LD = R + 1;           // padded tile row (one column c)
-  constexpr int ES = NX * LD;         // envelope offset in the tile
+  constexpr int ES = NX * R;          // envelope offset in the tile
   constexpr int HALF = R / 2;         // float4 (two y values) per column segment
   constexpr int VEC = 2 * NX * HALF / kRowThreads;
   static_assert(VEC * kRowThreads == 2 * NX * HALF, "tile split");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* tile = reinterpret_cast<float2*>(smem_raw);  // [env][NX][LD]
+  float2* tile = reinterpret_cast<float2*>(smem_raw);  // [env][NX][R], swizzled (tile_at)
   const int g = threadIdx.x / T;
   const int t = threadIdx.x % T;
   const int ch = blockIdx.y;
   const int y0 = blockIdx.x * R;
   const int y = y0 + g;
   const size_t chb = size_t(ch) * A.ny * NX;
-  float2* rowbuf = tile + g;  // this row's exchange column, stride LD, envelopes ES apart
   float2 a[16], b[16];
   if constexpr (MODE == 0) {
     const float2* e0 = A.e0 + chb + size_t(y) * NX;
@@ -199,17 +224,17 @@ __global__ void __launch_bounds__(RT, 512 / RT) row_pass_kernel(Pass3DArgs A) {
       const int e = i / (NX * HALF);
       const int c = (i / HALF) % NX;
       const int h = i % HALF;
-      float2* d = tile + e * ES + c * LD + 2 * h;
-      d[0] = make_float2(v[j].x, v[j].y);
-      d[1] = make_float2(v[j].z, v[j].w);
+      float2* d = tile + e * ES;
+      d[tile_at<R>(c, 2 * h)] = make_float2(v[j].x, v[j].y);
+      d[tile_at<R>(c, 2 * h + 1)] = make_float2(v[j].z, v[j].w);
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
-      a[k] = rowbuf[(k * T + t) * LD];
-      b[k] = rowbuf[ES + (k * T + t) * LD];
+      a[k] = tile[tile_at<R>(k * T + t, g)];
+      b[k] = tile[ES + tile_at<R>(k * T + t, g)];
     }
-    Fft2Env<NX>::inv(a, b, rowbuf, LD, ES, A.twx, t, g);
+    Fft2Env<NX>::template inv<R>(a, b, tile, 0, ES, A.twx, t, g);
     const float2* crow = A.cfield + (size_t(A.z) * A.ny + y) * NX;
     const ChannelCoef cf = A.coef[ch];
 #pragma unroll
@@ -239,12 +264,12 @@ __global__ void __launch_bounds__(RT, 512 / RT) row_pass_kernel(Pass3DArgs A) {
       eh[t + T * k] = b[k];
     }
   } else {
-    Fft2Env<NX>::fwd(a, b, rowbuf, LD, ES, A.twx, t, g);
+    Fft2Env<NX>::template fwd<R>(a, b, tile, 0, ES, A.twx, t, g);
     g3_sync<T>(g);
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
-      rowbuf[(k * T + t) * LD] = a[k];
-      rowbuf[ES + (k * T + t) * LD] = b[k];
+      tile[tile_at<R>(k * T + t, g)] = a[k];
+      tile[ES + tile_at<R>(k * T + t, g)] = b[k];
     }
     __syncthreads();
     float4 v[VEC];
@@ -254,8 +279,9 @@ __global__ void __launch_bounds__(RT, 512 / RT) row_pass_kernel(Pass3DArgs A) {
       const int e = i / (NX * HALF);
       const int c = (i / HALF) % NX;
       const int h = i % HALF;
-      const float2* d = tile + e * ES + c * LD + 2 * h;
-      v[j] = make_float4(d[0].x, d[0].y, d[1].x, d[1].y);
+      const float2* d = tile + e * ES;
+      const float2 lo = d[tile_at<R>(c, 2 * h)], hi = d[tile_at<R>(c, 2 * h + 1)];
+      v[j] = make_float4(lo.x, lo.y, hi.x, hi.y);
     }
 #pragma unroll
     for (int j = 0; j < VEC; ++j) {
@@ -351,7 +377,7 @@ __global__ void reduce3d_kernel(const float2* e0, const float2* eh, long long pl
 
 template <int NX, int RT>
 size_t row_smem() {
-  return size_t(2) * NX * (RT / (NX / 16) + 1) * sizeof(float2);
+  return size_t(2) * NX * (RT / (NX / 16)) * sizeof(float2);
 }
 
 template <int NY>

@@ -16,8 +16,9 @@
 // FFT's registers (thread t holds px = 16 t + k at c = k T + t).  Columns are
 // then contiguous for the column pass, which loads them straight into
 // registers; the row pass does the transposition: a block of R rows stages its
-// [c][R + 1] tile in shared memory (64-byte segments per column in HBM), and
-// each row's FFT exchanges through its own tile column.  A run of n steps is
+// [c][R] tile in shared memory (R x 8-byte segments per column in HBM), both
+// envelopes of an element side by side in one 16-byte slot, and each row's FFT
+// exchanges through its own tile column.  A run of n steps is
 // one row pass (forward x of the natural-order fields), then n x (column pass,
 // row pass); the last row pass writes natural [ch][y][x] order.  Traffic:
 // 2 passes x 2 envelopes x (8 B read + 8 B write) = 64 B per cell-update.
@@ -48,12 +49,16 @@ BPM_DEV void g3_sync(int g) {
 }
 
 // Row-pass tile of R rows: element (c, r) (transposed-spectrum column c, tile
-// row r) of an envelope at c R + (r ^ tile_swz<R>(c)).  The XOR spreads every
-// 16-thread phase of the pass's 64-bit accesses over distinct banks: the
-// column-segment staging, the row reads and writes, and the FFT exchanges.
+// row r) at 16-byte slot c R + (r ^ tile_swz<R>(c)), holding (E0, Eh).  Every
+// access of the pass to the tile is 128-bit, so a warp splits into 8-thread
+// phases; the XOR keeps each phase on distinct 16-byte bank groups for the
+// column-segment staging, the row reads and writes, and the FFT exchanges
+// (these place 8 consecutive threads on columns that differ in their low three
+// bits, which the XOR maps to distinct slots mod 8).
 template <int R>
 __host__ __device__ constexpr int tile_swz(int c) {
-  return R <= 16 ? (c / (16 / R)) % R : c % 16;
+  static_assert(R >= 4, "row tiles of at least 4 rows");
+  return R >= 8 ? c % 8 : (c >> 1) % 4;
 }
 template <int R>
 BPM_DEV int tile_at(int c, int r) {
@@ -97,22 +102,38 @@ struct Fft2Env {
     }
   }
 
+  // TR > 0: buf is the row-pass tile of 16-byte (E0, Eh) slots.
   template <int SF, int ST, int TR>
   static BPM_DEV void xchg(float2 (&a)[16], float2 (&b)[16], float2* buf, int stride, int estride,
                            int t, int g) {
     g3_sync<T>(g);
+    if constexpr (TR > 0) {
+      float4* q = reinterpret_cast<float4*>(buf);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const int p = slot<TR>(Gm::template pos<SF>(t, k), stride, g);
-      buf[p] = a[k];
-      buf[p + estride] = b[k];
-    }
-    g3_sync<T>(g);
+      for (int k = 0; k < 16; ++k)
+        q[slot<TR>(Gm::template pos<SF>(t, k), stride, g)] =
+            make_float4(a[k].x, a[k].y, b[k].x, b[k].y);
+      g3_sync<T>(g);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const int p = slot<TR>(Gm::template pos<ST>(t, k), stride, g);
-      a[k] = buf[p];
-      b[k] = buf[p + estride];
+      for (int k = 0; k < 16; ++k) {
+        const float4 v = q[slot<TR>(Gm::template pos<ST>(t, k), stride, g)];
+        a[k] = make_float2(v.x, v.y);
+        b[k] = make_float2(v.z, v.w);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int p = slot<TR>(Gm::template pos<SF>(t, k), stride, g);
+        buf[p] = a[k];
+        buf[p + estride] = b[k];
+      }
+      g3_sync<T>(g);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int p = slot<TR>(Gm::template pos<ST>(t, k), stride, g);
+        a[k] = buf[p];
+        b[k] = buf[p + estride];
+      }
     }
   }
 
@@ -185,12 +206,11 @@ __global__ void __launch_bounds__(RT, 512 / RT) row_pass_kernel(Pass3DArgs A) {
   constexpr int kRowThreads = RT;
   constexpr int T = NX / 16;
   constexpr int R = kRowThreads / T;  // rows per block
-  constexpr int ES = NX * R;          // envelope offset in the tile
   constexpr int HALF = R / 2;         // float4 (two y values) per column segment
-  constexpr int VEC = 2 * NX * HALF / kRowThreads;
-  static_assert(VEC * kRowThreads == 2 * NX * HALF, "tile split");
+  constexpr int VEC = NX * HALF / kRowThreads;  // segment pieces per thread and envelope
+  static_assert(VEC * kRowThreads == NX * HALF, "tile split");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* tile = reinterpret_cast<float2*>(smem_raw);  // [env][NX][R], swizzled (tile_at)
+  float4* tile = reinterpret_cast<float4*>(smem_raw);  // [NX][R] (E0, Eh) slots, swizzled (tile_at)
   const int g = threadIdx.x / T;
   const int t = threadIdx.x % T;
   const int ch = blockIdx.y;
@@ -207,34 +227,37 @@ __global__ void __launch_bounds__(RT, 512 / RT) row_pass_kernel(Pass3DArgs A) {
       b[k] = eh[t + T * k];
     }
   } else {
-    // transposed load: column c, rows y0 .. y0 + R - 1 (R x 8 bytes contiguous)
-    float4 v[VEC];
+    // transposed load: column c, rows y0 .. y0 + R - 1 (R x 8 bytes contiguous),
+    // piece h = rows 2h, 2h + 1 of both envelopes
+    float4 v0[VEC], v1[VEC];
 #pragma unroll
     for (int j = 0; j < VEC; ++j) {
       const int i = threadIdx.x + j * kRowThreads;
-      const int e = i / (NX * HALF);
-      const int c = (i / HALF) % NX;
-      const int h = i % HALF;
-      const float2* src = (e == 0 ? A.s0 : A.sh) + chb + size_t(c) * A.ny + y0 + 2 * h;
-      v[j] = __ldg(reinterpret_cast<const float4*>(src));
+      const size_t off = chb + size_t(i / HALF) * A.ny + y0 + 2 * (i % HALF);
+      v0[j] = __ldg(reinterpret_cast<const float4*>(A.s0 + off));
+      v1[j] = __ldg(reinterpret_cast<const float4*>(A.sh + off));
     }
 #pragma unroll
     for (int j = 0; j < VEC; ++j) {
       const int i = threadIdx.x + j * kRowThreads;
-      const int e = i / (NX * HALF);
-      const int c = (i / HALF) % NX;
+      const int c = i / HALF;
       const int h = i % HALF;
-      float2* d = tile + e * ES;
-      d[tile_at<R>(c, 2 * h)] = make_float2(v[j].x, v[j].y);
-      d[tile_at<R>(c, 2 * h + 1)] = make_float2(v[j].z, v[j].w);
+      // pieces 4..7 of every 8 store their odd row first: that keeps both
+      // stores of an 8-thread phase on distinct bank groups when R >= 16
+      const int sw = (h >> 2) & 1;
+      const float4 lo = make_float4(v0[j].x, v0[j].y, v1[j].x, v1[j].y);
+      const float4 hi = make_float4(v0[j].z, v0[j].w, v1[j].z, v1[j].w);
+      tile[tile_at<R>(c, 2 * h + sw)] = sw ? hi : lo;
+      tile[tile_at<R>(c, 2 * h + 1 - sw)] = sw ? lo : hi;
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
-      a[k] = tile[tile_at<R>(k * T + t, g)];
-      b[k] = tile[ES + tile_at<R>(k * T + t, g)];
+      const float4 v = tile[tile_at<R>(k * T + t, g)];
+      a[k] = make_float2(v.x, v.y);
+      b[k] = make_float2(v.z, v.w);
     }
-    Fft2Env<NX>::template inv<R>(a, b, tile, 0, ES, A.twx, t, g);
+    Fft2Env<NX>::template inv<R>(a, b, reinterpret_cast<float2*>(tile), 0, 0, A.twx, t, g);
     const float2* crow = A.cfield + (size_t(A.z) * A.ny + y) * NX;
     const ChannelCoef cf = A.coef[ch];
 #pragma unroll
@@ -264,33 +287,31 @@ __global__ void __launch_bounds__(RT, 512 / RT) row_pass_kernel(Pass3DArgs A) {
       eh[t + T * k] = b[k];
     }
   } else {
-    Fft2Env<NX>::template fwd<R>(a, b, tile, 0, ES, A.twx, t, g);
+    Fft2Env<NX>::template fwd<R>(a, b, reinterpret_cast<float2*>(tile), 0, 0, A.twx, t, g);
     g3_sync<T>(g);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      tile[tile_at<R>(k * T + t, g)] = a[k];
-      tile[ES + tile_at<R>(k * T + t, g)] = b[k];
-    }
+    for (int k = 0; k < 16; ++k)
+      tile[tile_at<R>(k * T + t, g)] = make_float4(a[k].x, a[k].y, b[k].x, b[k].y);
     __syncthreads();
-    float4 v[VEC];
+    float4 v0[VEC], v1[VEC];
 #pragma unroll
     for (int j = 0; j < VEC; ++j) {
       const int i = threadIdx.x + j * kRowThreads;
-      const int e = i / (NX * HALF);
-      const int c = (i / HALF) % NX;
+      const int c = i / HALF;
       const int h = i % HALF;
-      const float2* d = tile + e * ES;
-      const float2 lo = d[tile_at<R>(c, 2 * h)], hi = d[tile_at<R>(c, 2 * h + 1)];
-      v[j] = make_float4(lo.x, lo.y, hi.x, hi.y);
+      const int sw = (h >> 2) & 1;
+      const float4 p = tile[tile_at<R>(c, 2 * h + sw)];
+      const float4 q = tile[tile_at<R>(c, 2 * h + 1 - sw)];
+      const float4 lo = sw ? q : p, hi = sw ? p : q;
+      v0[j] = make_float4(lo.x, lo.y, hi.x, hi.y);
+      v1[j] = make_float4(lo.z, lo.w, hi.z, hi.w);
     }
 #pragma unroll
     for (int j = 0; j < VEC; ++j) {
       const int i = threadIdx.x + j * kRowThreads;
-      const int e = i / (NX * HALF);
-      const int c = (i / HALF) % NX;
-      const int h = i % HALF;
-      float2* dst = (e == 0 ? A.s0 : A.sh) + chb + size_t(c) * A.ny + y0 + 2 * h;
-      *reinterpret_cast<float4*>(dst) = v[j];
+      const size_t off = chb + size_t(i / HALF) * A.ny + y0 + 2 * (i % HALF);
+      *reinterpret_cast<float4*>(A.s0 + off) = v0[j];
+      *reinterpret_cast<float4*>(A.sh + off) = v1[j];
     }
   }
 }

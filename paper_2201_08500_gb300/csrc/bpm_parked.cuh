@@ -360,7 +360,13 @@ struct Parked {
     float2* ph = p0 + N;
     double* red = reinterpret_cast<double*>(ph + N);
     const float4* gtab = A.tables + size_t(ch) * kTabs * 2 * N;
-    const ChannelCoef cf = A.coef[size_t(ch) * kTabs];
+    // first order: the coupling coefficients are read from shared memory at
+    // each coupling instead of held in eight registers across the transforms
+    ChannelCoef* scf = reinterpret_cast<ChannelCoef*>(red + 32);
+    if (SPLIT == 1 && t == 0) scf[0] = A.coef[ch];
+    __syncthreads();
+    const ChannelCoef cfr = A.coef[size_t(ch) * kTabs];
+    const ChannelCoef& cf = SPLIT == 1 ? scf[0] : cfr;
     const float4* tw = reinterpret_cast<const float4*>(kWide ? A.twiddle_p : A.twiddle_t);
     float2* e0 = A.e0 + size_t(ch) * N;
     float2* eh = A.eh + size_t(ch) * N;

@@ -122,3 +122,19 @@ def test_3d_asymmetric_cut_matches_oracle():
     w.tan_psi = math.tan(math.radians(7.0))
     e0, eh, _ = gpu(w)
     check(w, e0, eh)
+
+
+def test_3d_zero_steps_return_the_incident_field():
+    """The empty 3D march: run(0) leaves E0 at the incident beam and Eh at zero."""
+    w = case3d(256, 256, 8, 2, seed=9)
+    p = bpm.plan_from_workload(w)
+    p.run(0)
+    p.sync()
+    e0, eh = p.e0(), p.eh()
+    R, T, rint = p.reflectivity()
+    _, _, init = orc.run(w, n_steps=0)
+    inc = np.linalg.norm(init, axis=1)
+    assert np.max(np.linalg.norm(e0.reshape(init.shape) - init, axis=1) / inc) < 1e-6
+    assert not np.any(eh) and not np.any(R) and rint == 0.0
+    assert np.max(np.abs(T - 1.0)) < 1e-6
+    p.close()

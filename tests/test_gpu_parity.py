@@ -270,3 +270,29 @@ def test_strain_gradient_benchmark(stream):
     p0 = np.sum(np.abs(e["init"][0]) ** 2)
     trans = np.sum(inten[x >= w.meta["x_back"]]) / p0
     assert abs(trans / w.meta["interbranch"] - 1.0) < 1.5e-3, trans
+
+
+@pytest.mark.parametrize("form", [0, 3])
+def test_zero_steps_return_the_incident_field(stream, form):
+    """The empty march: run(0) leaves E0 at the incident beam (Section 3.1) and
+    Eh at zero, so R = 0 and T = 1; the remaining steps then give the full
+    march.  A plan of no channels is refused."""
+    w = deformed_small(2048, nz=30, n_ch=3, seed=5)
+    p = bpm.plan_from_workload(w, stream=stream)
+    p.set_launch(form=form, channels_per_block=1)
+    p.run(0)
+    p.sync()
+    e0, eh = p.e0(), p.eh()
+    R, T, rint = p.reflectivity()
+    _, _, init = orc.run(w, n_steps=0)
+    inc = np.linalg.norm(init, axis=1)
+    assert np.max(np.linalg.norm(e0 - init, axis=1) / inc) < 1e-6
+    assert not np.any(eh) and not np.any(R) and rint == 0.0
+    assert np.max(np.abs(T - 1.0)) < 1e-6
+    p.run(w.nz)
+    p.sync()
+    e = errors(w, dict(e0=p.e0(), eh=p.eh()))
+    assert e["per_ch"] < TOL_FIELD, e
+    p.close()
+    with pytest.raises(bpm.BpmError):
+        bpm.Plan(2, 256, 1, 10, 0.5e-6, 0, 0.5e-6, 0, stream=stream)

@@ -42,7 +42,6 @@ METRIC = "BPM cell-updates/s (omega*x*z)"
 # configuration reports null.
 MEASURED_TRAFFIC = {
     ("march_kernel<4096,1> form 0", "deformed-2d-nx4096-nz2000-ch1024", 1): 660.43e6,
-    ("march_kernel<4096,1> form 3", "deformed-2d-nx4096-nz2000-ch1024", 1): 587.53e6,
 }
 UNIT = "cell-updates/s"
 FP32_LANES_PER_SM = 128

@@ -15,8 +15,17 @@
 // element is that of bpm_resident.cuh (same butterflies, twiddles, tables and
 // coupling, in the same order), so the fields are bitwise the same.
 //
-// Shared memory: exchange buffer (padded, N + N/16 complex64), E0 park, Eh park
-// (N complex64 each) and the reduction area: 196.5 KB.  Tables and stage twiddles are read from L2.
+// Shared memory: exchange buffer, E0 park and Eh park (N + N/16 complex64 each,
+// the padded exchange size) and the reduction area: 209.4 KB at 8192.  Tables
+// and stage twiddles are read from L2 (or TMEM).
+//
+// Barriers: an envelope's transform alternates its exchanges between the park
+// area that is free while it runs and the exchange buffer (park, buffer, park,
+// buffer).  Each exchange then needs one block barrier (between its stores and
+// its loads) instead of two: the barrier of exchange i + 1 already orders every
+// thread's loads of exchange i before anyone stores into that buffer again at
+// exchange i + 2.  A step adds one barrier at its start and one between the
+// parking and the second transform, 10 barriers instead of 16.
 //
 // States of a step: [E0 in v, Eh parked] -> propagate E0 -> park E0, take Eh
 // -> propagate Eh -> [Eh in v, E0 parked] -> couple (reading E0 back) ->
@@ -52,11 +61,10 @@ struct Parked {
   static constexpr bool kWide = WIDE;
 
   __host__ __device__ static constexpr size_t xbuf_bytes() { return size_t(Pad<N>::kSlots) * sizeof(float2); }
-  __host__ __device__ static constexpr size_t vec_bytes() { return size_t(N) * sizeof(float2); }
   __host__ __device__ static constexpr size_t red_bytes() { return 64 * sizeof(double); }
-  __host__ __device__ static constexpr size_t smem_bytes() {
-    return xbuf_bytes() + 2 * vec_bytes() + red_bytes();
-  }
+  // The parks have the exchange buffer's padded size: each serves as the
+  // second exchange buffer of the other envelope's transform.
+  __host__ __device__ static constexpr size_t smem_bytes() { return 3 * xbuf_bytes() + red_bytes(); }
 
   // Per-element stage twiddles (twiddle_order on the host): stage s, output m
   // of thread t at tw_off(s) + (m - 1) LN(s) + t % LN(s).
@@ -124,12 +132,12 @@ struct Parked {
   }
 
   // Single-envelope exchange through the padded layout (Pad<N>, 64-bit slots).
+  // No leading barrier: no thread may still be reading x (see propagate).
   template <int SF, int ST>
   static BPM_DEV void exchange(float2 (&v)[16], float2* x, int t) {
     using P = Pad<N>;
     float2* st = x + P::template base<SF>(t);
     const float2* ld = x + P::template base<ST>(t);
-    __syncthreads();
 #pragma unroll
     for (int k = 0; k < 16; ++k) st[P::template off<SF>(k)] = v[k];
     __syncthreads();
@@ -179,13 +187,16 @@ struct Parked {
     }
   }
 
-  static BPM_DEV void propagate(float2 (&v)[16], float2* x, const float4* gt, uint32_t tcol,
-                                const float4* tw, int t) {
-    static_assert(S == 3 || S == 4, "parked form: 1024 <= N <= 8192");
+  // The four exchanges alternate xa, xb, xa, xb.  On entry no thread may still
+  // be reading xa or have reads of xb pending behind the first exchange's
+  // barrier; on return xa is free and other threads may still load from xb.
+  static BPM_DEV void propagate(float2 (&v)[16], float2* xa, float2* xb, const float4* gt,
+                                uint32_t tcol, const float4* tw, int t) {
+    static_assert(S == 3 || (S == 4 && kPairLast), "parked form: 1024 <= N <= 8192, 4 exchanges");
     stage_fwd<0>(v, tw, t);
-    exchange<0, 1>(v, x, t);
+    exchange<0, 1>(v, xa, t);
     stage_fwd<1>(v, tw, t);
-    exchange<1, 2>(v, x, t);
+    exchange<1, 2>(v, xb, t);
     stage_fwd<2>(v, tw, t);
     if constexpr (kPairLast) {
       pair_swap(v, t);
@@ -205,20 +216,12 @@ struct Parked {
       }
       pair_swap(v, t);
     } else {
-      if constexpr (S == 4) {
-        exchange<2, 3>(v, x, t);
-        stage_fwd<3>(v, tw, t);
-      }
       multiply(v, gt, tcol, t);
-      if constexpr (S == 4) {
-        stage_inv<3>(v, tw, t);
-        exchange<3, 2>(v, x, t);
-      }
     }
     stage_inv<2>(v, tw, t);
-    exchange<2, 1>(v, x, t);
+    exchange<2, 1>(v, xa, t);
     stage_inv<1>(v, tw, t);
-    exchange<1, 0>(v, x, t);
+    exchange<1, 0>(v, xb, t);
     stage_inv<0>(v, tw, t);
   }
 
@@ -262,12 +265,17 @@ struct Parked {
   }
 
   // [E0 in v, Eh parked] -> [Eh in v, E0 parked], both propagated (table set gt).
+  // Before: each thread's last accesses of p0 and ph were to its own slots.
+  // After: p0 and ph hold the parked E0 and (free) slots of Eh; other threads
+  // may still load from x.
   static BPM_DEV void propagate_both(float2 (&v)[16], float2* x, float2* p0, float2* ph,
                                      const float4* gt, uint32_t tcol, const float4* tw, int t) {
-    propagate(v, x, gt, tcol, tw, t);
+    __syncthreads();  // own-slot accesses of p0 / ph and loads of x are done
+    propagate(v, p0, x, gt, tcol, tw, t);  // p0 is free while E0 is in registers
     park(v, p0, t);
     unpark(v, ph, t);
-    propagate(v, x, gt + N, tcol + 64u, tw, t);
+    __syncthreads();  // x loads and the unparking of ph are done
+    propagate(v, ph, x, gt + N, tcol + 64u, tw, t);
   }
 
   // [Eh in v, E0 parked] -> coupling at z_n -> [E0 in v, Eh parked].
@@ -357,8 +365,8 @@ struct Parked {
                                     uint32_t tcol = 0) {
     float2* x = reinterpret_cast<float2*>(smem);
     float2* p0 = x + Pad<N>::kSlots;
-    float2* ph = p0 + N;
-    double* red = reinterpret_cast<double*>(ph + N);
+    float2* ph = p0 + Pad<N>::kSlots;
+    double* red = reinterpret_cast<double*>(ph + Pad<N>::kSlots);
     const float4* gtab = A.tables + size_t(ch) * kTabs * 2 * N;
     // first order: the coupling coefficients are read from shared memory at
     // each coupling instead of held in eight registers across the transforms

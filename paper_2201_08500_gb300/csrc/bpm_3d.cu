@@ -17,8 +17,9 @@
 // then contiguous for the column pass, which loads them straight into
 // registers; the row pass does the transposition: a block of R rows stages its
 // [c][R] tile in shared memory (R x 8-byte segments per column in HBM), both
-// envelopes of an element side by side in one 16-byte slot, and each row's FFT
-// exchanges through its own tile column.  A run of n steps is
+// envelopes of an element side by side in one 16-byte slot.  Between reading
+// the tile and rewriting it, each row's transforms exchange through the row's
+// own padded region of the same shared memory.  A run of n steps is
 // one row pass (forward x of the natural-order fields), then n x (column pass,
 // row pass); the last row pass writes natural [ch][y][x] order.  Traffic:
 // 2 passes x 2 envelopes x (8 B read + 8 B write) = 64 B per cell-update.
@@ -52,9 +53,9 @@ BPM_DEV void g3_sync(int g) {
 // row r) at 16-byte slot c R + (r ^ tile_swz<R>(c)), holding (E0, Eh).  Every
 // access of the pass to the tile is 128-bit, so a warp splits into 8-thread
 // phases; the XOR keeps each phase on distinct 16-byte bank groups for the
-// column-segment staging, the row reads and writes, and the FFT exchanges
-// (these place 8 consecutive threads on columns that differ in their low three
-// bits, which the XOR maps to distinct slots mod 8).
+// column-segment staging and the row reads and writes (these place 8
+// consecutive threads on consecutive columns, which the XOR maps to distinct
+// slots mod 8).
 template <int R>
 __host__ __device__ constexpr int tile_swz(int c) {
   static_assert(R >= 4, "row tiles of at least 4 rows");
@@ -91,46 +92,40 @@ struct Fft2Env {
     }
   }
 
-  // Slot of position p: TR = 0, swz(p) * stride; TR > 0, the row-pass tile of
-  // TR rows with this group's row g (buf is then the tile base).
-  template <int TR>
-  static BPM_DEV int slot(int p, int stride, int g) {
-    if constexpr (TR > 0) {
-      return tile_at<TR>(swz(p), g);
-    } else {
-      return swz(p) * stride;
-    }
-  }
-
-  // TR > 0: buf is the row-pass tile of 16-byte (E0, Eh) slots.
+  // TR = 0: element p of envelope e at buf[swz(p) * stride + e * estride]
+  // (the column pass).  TR < 0: buf is this group's own region of
+  // Pad<N>::kSlots 16-byte (E0, Eh) slots in the padded layout, one base
+  // register per pattern and compile-time offsets (the row pass).
   template <int SF, int ST, int TR>
   static BPM_DEV void xchg(float2 (&a)[16], float2 (&b)[16], float2* buf, int stride, int estride,
                            int t, int g) {
     g3_sync<T>(g);
-    if constexpr (TR > 0) {
+    if constexpr (TR < 0) {
       float4* q = reinterpret_cast<float4*>(buf);
+      float4* st = q + Pad<N>::template base<SF>(t);
 #pragma unroll
       for (int k = 0; k < 16; ++k)
-        q[slot<TR>(Gm::template pos<SF>(t, k), stride, g)] =
-            make_float4(a[k].x, a[k].y, b[k].x, b[k].y);
+        st[Pad<N>::template off<SF>(k)] = make_float4(a[k].x, a[k].y, b[k].x, b[k].y);
       g3_sync<T>(g);
+      const float4* ld = q + Pad<N>::template base<ST>(t);
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
-        const float4 v = q[slot<TR>(Gm::template pos<ST>(t, k), stride, g)];
+        const float4 v = ld[Pad<N>::template off<ST>(k)];
         a[k] = make_float2(v.x, v.y);
         b[k] = make_float2(v.z, v.w);
       }
     } else {
+      static_assert(TR == 0, "exchange layout");
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
-        const int p = slot<TR>(Gm::template pos<SF>(t, k), stride, g);
+        const int p = swz(Gm::template pos<SF>(t, k)) * stride;
         buf[p] = a[k];
         buf[p + estride] = b[k];
       }
       g3_sync<T>(g);
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
-        const int p = slot<TR>(Gm::template pos<ST>(t, k), stride, g);
+        const int p = swz(Gm::template pos<ST>(t, k)) * stride;
         a[k] = buf[p];
         b[k] = buf[p + estride];
       }
@@ -161,8 +156,8 @@ struct Fft2Env {
     }
   }
 
-  // natural layout (pos<0>) -> digit-reversed spectrum (pos<S-1>).  TR > 0:
-  // exchanges through the row-pass tile of TR rows (see slot).
+  // natural layout (pos<0>) -> digit-reversed spectrum (pos<S-1>); TR selects
+  // the exchange layout (see xchg).
   template <int TR = 0>
   static BPM_DEV void fwd(float2 (&a)[16], float2 (&b)[16], float2* buf, int stride, int estride,
                           const float2* tw, int t, int g) {
@@ -212,6 +207,9 @@ __global__ void __launch_bounds__(RT, 512 / RT) row_pass_kernel(Pass3DArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* tile = reinterpret_cast<float4*>(smem_raw);  // [NX][R] (E0, Eh) slots, swizzled (tile_at)
   const int g = threadIdx.x / T;
+  // row g's exchange region (Pad<NX>::kSlots 16-byte slots), overlapping the
+  // tile: the transforms run between the tile's read and its rewrite
+  float2* xrow = reinterpret_cast<float2*>(tile + size_t(g) * Pad<NX>::kSlots);
   const int t = threadIdx.x % T;
   const int ch = blockIdx.y;
   const int y0 = blockIdx.x * R;
@@ -257,7 +255,8 @@ __global__ void __launch_bounds__(RT, 512 / RT) row_pass_kernel(Pass3DArgs A) {
       a[k] = make_float2(v.x, v.y);
       b[k] = make_float2(v.z, v.w);
     }
-    Fft2Env<NX>::template inv<R>(a, b, reinterpret_cast<float2*>(tile), 0, 0, A.twx, t, g);
+    __syncthreads();  // the rows' exchange regions overlap the tile
+    Fft2Env<NX>::template inv<-1>(a, b, xrow, 0, 0, A.twx, t, g);
     const float2* crow = A.cfield + (size_t(A.z) * A.ny + y) * NX;
     const ChannelCoef cf = A.coef[ch];
 #pragma unroll
@@ -287,8 +286,8 @@ __global__ void __launch_bounds__(RT, 512 / RT) row_pass_kernel(Pass3DArgs A) {
       eh[t + T * k] = b[k];
     }
   } else {
-    Fft2Env<NX>::template fwd<R>(a, b, reinterpret_cast<float2*>(tile), 0, 0, A.twx, t, g);
-    g3_sync<T>(g);
+    Fft2Env<NX>::template fwd<-1>(a, b, xrow, 0, 0, A.twx, t, g);
+    __syncthreads();  // every row is done with its exchange region
 #pragma unroll
     for (int k = 0; k < 16; ++k)
       tile[tile_at<R>(k * T + t, g)] = make_float4(a[k].x, a[k].y, b[k].x, b[k].y);
@@ -396,9 +395,11 @@ __global__ void reduce3d_kernel(const float2* e0, const float2* eh, long long pl
   }
 }
 
+// The larger of the tile (NX x R slots) and the rows' exchange regions
+// (R x Pad<NX>::kSlots slots), 16 bytes a slot.
 template <int NX, int RT>
 size_t row_smem() {
-  return size_t(2) * NX * (RT / (NX / 16)) * sizeof(float2);
+  return size_t(RT / (NX / 16)) * Pad<NX>::kSlots * sizeof(float4);
 }
 
 template <int NY>

@@ -11,8 +11,11 @@ cell-updates per second (channel x transverse cell x z step).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 N > 1 runs under torchrun: every rank marches an independent instance of the
-same size (weak scaling); there is no data-path collective.  --impl reference
-times the FP64 CPU oracle on the host cores on a bounded channel sample.
+same size (weak scaling); there is no data-path collective.  With
+--shard-channels the ranks instead split one instance's channels into
+contiguous blocks and sum-reduce its time response, the one exchange of a
+sharded pulse (strong scaling).  --impl reference times the FP64 CPU oracle on
+the host cores on a bounded channel sample.
 """
 from __future__ import annotations
 
@@ -461,6 +464,10 @@ def main():
     ap.add_argument("--requests", type=int, default=10000,
                     help="served: number of requests (80 % rocking-curve probes)")
     ap.add_argument("--load", type=float, default=0.7, help="served: offered load / capacity")
+    ap.add_argument("--shard-channels", action="store_true",
+                    help="deformed workload: the ranks split ONE instance's channels and "
+                         "sum-reduce its time response (strong scaling) instead of each "
+                         "marching its own instance")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if args.impl == "reference":
@@ -486,7 +493,16 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    w = rank_workload(args.channels, args.nx, args.nz, rank)
+    from paper_2201_08500_gb300 import shard
+    w_all = None  # the sharded instance (--shard-channels)
+    if args.shard_channels:
+        w_all = workloads.deformed(n_ch=args.channels, nx=args.nx, nz=args.nz, seed=2)
+        first, cnt = shard.channel_blocks(w_all.n_ch, world)[rank]
+        if cnt == 0:
+            raise SystemExit("--shard-channels needs at least one channel per rank")
+        w = w_all.subset(list(range(first, first + cnt)))
+    else:
+        w = rank_workload(args.channels, args.nx, args.nz, rank)
     w.split_order = args.split_order
     stream = torch.cuda.current_stream()
     u_dev = torch.from_numpy(np.ascontiguousarray(w.u)).cuda()
@@ -500,6 +516,9 @@ def main():
     plan = bpm.Plan(w.dims, w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.n_ch, stream=stream,
                     zassenhaus=w.zassenhaus, split_order=w.split_order)
     plan.set_timing(True)
+    if w_all is not None:
+        plan.set_channel_shard(first, w_all.n_ch, shard.pulse_spacing(w_all.omega))
+        t_dev = torch.empty((w_all.n_ch, w.plane), dtype=torch.complex128, device="cuda")
     if args.launch_form is not None:
         plan.set_launch(form=args.launch_form,
                         channels_per_block=1 if args.launch_form >= 2 else None)
@@ -511,6 +530,10 @@ def main():
                          w.thickness, u=u)
         plan.set_pulse(omega, S, w.theta_i, w.x0, w.w0, w.zx, w.zR)
         plan.run()
+        if w_all is not None and world > 1:
+            # the one exchange of a sharded pulse: sum the time-response parts
+            plan.fetch(bpm.BPM_FIELD_EH_TIME, out=t_dev)
+            shard.combine(t_dev, 0.0)
 
     # L2 (129 MB) is flushed between timed steps by writing a 256 MB buffer
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
@@ -538,19 +561,25 @@ def main():
     ms_local = sum(step_ms) / len(step_ms)
     ms = max_over_ranks(ms_local, dist, device="cuda")
     cells_per_rank = w.cell_updates
-    value = whole_job_value(world, cells_per_rank, ms)
+    # whole-job cell-updates: every rank's instance, or the one sharded instance
+    job_cells = w_all.cell_updates if w_all is not None else world * cells_per_rank
+    value = whole_job_value(1, job_cells, ms)
 
     # end to end through the C ABI with host buffers: pinned u in, R and the
     # time response out, copies inside the timed region
     u_pin = torch.from_numpy(np.ascontiguousarray(w.u)).pin_memory()
-    t_host = torch.empty((w.n_ch, w.plane), dtype=torch.complex128).pin_memory()
+    t_rows = w_all.n_ch if w_all is not None else w.n_ch
+    t_host = torch.empty((t_rows, w.plane), dtype=torch.complex128).pin_memory()
     R = np.empty(w.n_ch)
     e2e_ms = []
     for i in range(max(2, min(args.steps, 5))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         step(u_pin)
-        plan.fetch(bpm.BPM_FIELD_EH_TIME, out=t_host)
+        if w_all is not None and world > 1:
+            t_host.copy_(t_dev)  # the reduced time response
+        else:
+            plan.fetch(bpm.BPM_FIELD_EH_TIME, out=t_host)
         R, _, _ = plan.reflectivity()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e = statistics.median(e2e_ms)
@@ -575,25 +604,31 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "higher_is_better": True, "scaling": "strong" if w_all is not None else "weak",
+            "vs_baseline": None,
             "dtype": "c64 fields / f32 butterflies (f64 setup and time sum)",
             "data": "synthetic",
-            "config": {"workload": w.name, "nx": w.nx, "nz": w.nz, "channels": w.n_ch,
+            "config": {"workload": w.name, "nx": w.nx, "nz": w.nz,
+                       "channels": w_all.n_ch if w_all is not None else w.n_ch,
                        "split_order": w.split_order,
                        "crystal": "thermal bump u = A exp(-x'^2/w^2)(z/Z)^2",
                        "l2": "flushed between timed steps (256 MB write)",
-                       "parallelism": f"{world} x independent instance",
+                       "parallelism": (f"{world} x channel shard of one instance, time "
+                                       f"response sum-reduced" if w_all is not None
+                                       else f"{world} x independent instance"),
                        "launch": plan.launch(), "tuned": tried},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak,
-                         "traffic": MEASURED_TRAFFIC.get((kernel, w.name, w.split_order)),
+                         # the captured launch held the whole instance
+                         "traffic": (MEASURED_TRAFFIC.get((kernel, w.name, w.split_order))
+                                     if w_all is None or world == 1 else None),
                          "algorithmic_bytes": alg_bytes,
                          "kernel": kernel,
                          "flops_per_cell_update": flops_per_cell(n, w.split_order),
                          "march_ms": march_avg,
                          "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 "
                                        f"x {sm_max:.0f} MHz"},
-            "e2e": {"value": world * cells_per_rank / (e2e * 1e-3), "unit": UNIT,
+            "e2e": {"value": job_cells / (e2e * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": 5 * args.steps,
             "clocks": clocks,

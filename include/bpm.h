@@ -128,6 +128,26 @@ BPM_API bpm_status bpm_set_pulse(bpm_plan plan, const double* omega, const doubl
 BPM_API bpm_status bpm_set_fields(bpm_plan plan, const void* e0, const void* eh, int z_step,
                                   int on_device);
 
+/* Channel sharding of one pulse across plans, e.g. one per GPU. Section 3.3
+ * solves the frequency components as independent stationary problems. Only two
+ * sums combine them: the time response (Section 3.3) and R_int (Section 3.1).
+ *
+ * The call declares that this plan's n_channels channels are channels
+ * first .. first + n_channels - 1 of a pulse of n_total channels spaced
+ * d_omega. From then on:
+ *   - BPM_FIELD_EH_TIME has n_total rows and holds this shard's part of the
+ *     sum, i.e. the channels of the other shards count as zero;
+ *   - bpm_fetch_reflectivity's R_int is d_omega times this shard's sum of R_i.
+ * The shards' time responses and R_int add up (a sum-reduce) to those of one
+ * plan holding all n_total channels.
+ *
+ * Ownership: the plan grows its time-response buffer to n_total rows when
+ * needed.
+ * Errors: INVALID_ARG if first < 0, the shard does not fit in [0, n_total), or
+ * d_omega is not positive and finite; STATE if called after the march has
+ * started (z > 0); CUDA if the buffer cannot be grown. */
+BPM_API bpm_status bpm_set_channel_shard(bpm_plan plan, int first, int n_total, double d_omega);
+
 /* Advances every channel n_steps split steps (Eq. fov10) from the current z,
  * then computes per-channel reflectivity R_i = sum|A-|^2 / sum|A+(z=0)|^2 and
  * transmissivity T_i, and, when the march has reached nz, the time response
@@ -148,9 +168,11 @@ BPM_API bpm_status bpm_sync(bpm_plan plan);
 enum {
   BPM_FIELD_E0 = 0,     /* complex64  [n_channels][ny][nx], current z              */
   BPM_FIELD_EH = 1,     /* complex64  [n_channels][ny][nx], current z              */
-  BPM_FIELD_EH_TIME = 2 /* complex128 [n_time = n_channels][ny][nx]: psi_h(t_j, x) =
+  BPM_FIELD_EH_TIME = 2 /* complex128 [n_time][ny][nx]: psi_h(t_j, x) =
                            d_omega sum_i A-(omega_i, x) exp(-2 pi i (i - n/2) j / n),
-                           t_j = 2 pi j / (n d_omega), envelope about omega_{n/2}  */
+                           t_j = 2 pi j / (n d_omega), envelope about omega_{n/2};
+                           n = n_time = n_channels, or the shard's n_total (the sum
+                           then runs over the shard's channels only)             */
 };
 
 /* Copies one output into dst (bytes must equal its exact size) on the plan's

@@ -29,7 +29,7 @@ EXPORTS = ("bpm_plan_create", "bpm_set_crystal", "bpm_set_pulse", "bpm_set_field
            "bpm_noalloc_scratch_bytes", "bpm_noalloc_last_error", "bpm_set_stream",
            "bpm_set_geometry", "bpm_batch_set_max_blocks", "bpm_batch_pending",
            "bpm_batch_graph_kernels", "bpm_get_launch", "bpm_set_launch", "bpm_tune",
-           "bpm_tune_save", "bpm_tune_load", "bpm_tune_clear")
+           "bpm_tune_save", "bpm_tune_load", "bpm_tune_clear", "bpm_set_channel_shard")
 
 
 class BpmError(RuntimeError):
@@ -91,6 +91,7 @@ def load(path: str = LIB_PATH):
         "bpm_set_crystal": ([_P] + [_D] * 10 + [_P, _I], _I),
         "bpm_set_pulse": ([_P, _P, _P, _D, _D, _D, _D, _D], _I),
         "bpm_set_fields": ([_P, _P, _P, _I, _I], _I),
+        "bpm_set_channel_shard": ([_P, _I, _I, _D], _I),
         "bpm_run": ([_P, _I], _I),
         "bpm_sync": ([_P], _I),
         "bpm_set_stream": ([_P, _P], _I),
@@ -170,6 +171,7 @@ class Plan:
         self._L = load()
         self.dims, self.nx, self.ny, self.nz = int(dims), int(nx), int(ny), int(nz)
         self.n_channels = int(n_channels)
+        self.n_time = self.n_channels  # rows of the time response
         self.plane = self.nx * (self.ny if self.dims == 3 else 1)
         g = Grid(self.dims, self.nx, self.ny if self.dims == 3 else 1, self.nz, float(dx),
                  float(dy), float(dz), int(split_order), int(zassenhaus))
@@ -248,8 +250,16 @@ class Plan:
     def set_stream(self, stream):
         self._check(self._L.bpm_set_stream(self._h, _stream_handle(stream)))
 
+    def set_channel_shard(self, first: int, n_total: int, d_omega: float):
+        """This plan holds channels first .. first + n_channels - 1 of a pulse of
+        n_total channels spaced d_omega: its time response (n_total rows) and
+        R_int become this shard's parts of the sums (bpm_set_channel_shard)."""
+        self._check(self._L.bpm_set_channel_shard(self._h, int(first), int(n_total),
+                                                  float(d_omega)))
+        self.n_time = int(n_total)
+
     def fetch(self, which: int, out=None):
-        shape = (self.n_channels, self.plane)
+        shape = (self.n_time if which == BPM_FIELD_EH_TIME else self.n_channels, self.plane)
         if out is None:
             dt = np.complex128 if which == BPM_FIELD_EH_TIME else np.complex64
             out = np.empty(shape, dt)

@@ -228,6 +228,10 @@ struct bpm_plan_s {
   int z = 0;
   SetupArgs sa{};
   double domega = 1.0;
+  // channel shard: this plan holds channels shard_first .. + n_ch - 1 of
+  // shard_total (all of them unless bpm_set_channel_shard says otherwise)
+  bool sharded = false;
+  int shard_first = 0, shard_total = 0;
 
   // device buffers
   float2* cfield = nullptr;
@@ -263,6 +267,11 @@ struct bpm_plan_s {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bpm_stats stats{};
 };
+
+namespace {
+// Rows of the plan's time response: all channels of the shard's instance.
+int time_rows(const bpm_plan_s* p) { return p->sharded ? p->shard_total : p->n_ch; }
+}  // namespace
 
 namespace {
 
@@ -643,7 +652,7 @@ BPM_API bpm_status bpm_set_pulse(bpm_plan p, const double* omega, const double* 
   p->sa.w0 = w0;
   p->sa.zx = zx;
   p->sa.zR = zR;
-  p->domega = p->n_ch > 1 ? omega[1] - omega[0] : 1.0;
+  if (!p->sharded) p->domega = p->n_ch > 1 ? omega[1] - omega[0] : 1.0;
   BPM_CUDA(p, cudaMemcpyAsync(p->omega, omega, sizeof(double) * p->n_ch, cudaMemcpyHostToDevice,
                               p->stream),
            "upload omega");
@@ -652,6 +661,29 @@ BPM_API bpm_status bpm_set_pulse(bpm_plan p, const double* omega, const double* 
            "upload weights");
   BPM_CUDA(p, enqueue_pulse(p), "pulse setup kernels");
   p->have_pulse = true;
+  return BPM_OK;
+}
+
+BPM_API bpm_status bpm_set_channel_shard(bpm_plan p, int first, int n_total, double d_omega) {
+  if (!p) return fail(nullptr, BPM_ERR_INVALID_ARG, "null plan");
+  if (first < 0 || n_total < p->n_ch || first + p->n_ch > n_total)
+    return fail(p, BPM_ERR_INVALID_ARG, "shard must lie within [0, n_total)");
+  if (!(d_omega > 0.0) || !std::isfinite(d_omega))
+    return fail(p, BPM_ERR_INVALID_ARG, "d_omega must be positive and finite");
+  if (p->z != 0) return fail(p, BPM_ERR_STATE, "set the shard before the march starts");
+  const int rows = std::max(p->shard_total, p->n_ch);
+  if (n_total > rows) {
+    double2* t = nullptr;
+    BPM_CUDA(p, dalloc(&t, size_t(n_total) * p->plane), "alloc time response");
+    cudaFree(p->eh_time);
+    p->eh_time = t;
+    p->bytes += size_t(n_total - rows) * p->plane * sizeof(double2);
+  }
+  p->sharded = true;
+  p->shard_first = first;
+  p->shard_total = n_total;
+  p->domega = d_omega;
+  p->time_valid = false;
   return BPM_OK;
 }
 
@@ -739,7 +771,8 @@ BPM_API bpm_status bpm_run(bpm_plan p, int n_steps) {
   p->z += n_steps;
   p->time_valid = false;
   if (p->z == p->grid.nz) {
-    BPM_CUDA(p, launch_omega_to_t(p->n_ch, p->plane, p->domega, p->eh, p->eh_time, p->stream),
+    BPM_CUDA(p, launch_omega_to_t(time_rows(p), p->shard_first, p->n_ch, p->plane, p->domega,
+                                  p->eh, p->eh_time, p->stream),
              "omega-to-t kernel");
     ++launches;
     p->time_valid = true;
@@ -782,7 +815,7 @@ BPM_API bpm_status bpm_fetch_fields(bpm_plan p, int which, void* dst, size_t byt
     case BPM_FIELD_EH_TIME:
       if (!p->time_valid) return fail(p, BPM_ERR_STATE, "time response needs the march at nz");
       src = p->eh_time;
-      need = n * sizeof(double2);
+      need = size_t(time_rows(p)) * p->plane * sizeof(double2);
       break;
     default: return fail(p, BPM_ERR_INVALID_ARG, "unknown field selector");
   }
@@ -1234,7 +1267,8 @@ bpm_status enqueue_round(bpm_batch b, RoundSlot& r, int chunk) {
     p->z += steps[k];
     p->time_valid = false;
     if (p->z == p->grid.nz) {
-      BPM_BCUDA(b, launch_omega_to_t(p->n_ch, p->plane, p->domega, p->eh, p->eh_time, b->stream),
+      BPM_BCUDA(b, launch_omega_to_t(time_rows(p), p->shard_first, p->n_ch, p->plane, p->domega,
+                                     p->eh, p->eh_time, b->stream),
                 "omega-to-t kernel");
       p->time_valid = true;
       if (!e.done) BPM_BCUDA(b, cudaEventCreateWithFlags(&e.done, cudaEventDisableTiming), "event");

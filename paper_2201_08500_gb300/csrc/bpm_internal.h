@@ -156,7 +156,9 @@ cudaError_t launch_tables(const SetupArgs& sa, const double* omega, const double
                           cudaStream_t s);
 cudaError_t launch_incident(const SetupArgs& sa, const double* omega, const double2* weight,
                             float2* e0, float2* eh, double* inc_norm, cudaStream_t s);
-cudaError_t launch_omega_to_t(int n_ch, long long plane, double domega, const float2* eh,
-                              double2* out, cudaStream_t s);
+// Time response of channels first .. first + n_local - 1 of n_total ([n_total]
+// rows of plane values; the other channels count as zero).
+cudaError_t launch_omega_to_t(int n_total, int first, int n_local, long long plane,
+                              double domega, const float2* eh, double2* out, cudaStream_t s);
 
 }  // namespace bpm

@@ -265,12 +265,15 @@ __global__ void incident_kernel(SetupArgs sa, const double* __restrict__ omega,
 // Frequency-to-time, n a power of two: per block COLS columns of the
 // [n][plane] spectrum, FP64 radix-2 transform in shared memory (bit-reversed
 // load, log2 n butterfly passes), output scaled by d_omega exp(2 pi i (n/2) j / n).
+// The plan holds channels first .. first + n_local - 1 of the n (a channel
+// shard, or all of them); the others enter as zeros, so the output is this
+// shard's part of the sum.
 // The n/2 twiddles W^m = exp(-2 pi i m / n) are computed once per block into
 // shared memory; stage len uses W^(kk n / len) (the same double as
 // exp(-2 pi i kk / len): both arguments are exact binary fractions).
 constexpr int kCols = 8;
-__global__ void omega_to_t_fft_kernel(int n, int logn, long long plane, double domega,
-                                      const float2* __restrict__ eh, double2* out) {
+__global__ void omega_to_t_fft_kernel(int n, int logn, int first, int n_local, long long plane,
+                                      double domega, const float2* __restrict__ eh, double2* out) {
   extern __shared__ double2 sm[];  // [n][kCols], then the twiddles [n/2]
   double2* tw = sm + size_t(n) * kCols;
   const long long x0 = (long long)blockIdx.x * kCols;
@@ -284,8 +287,9 @@ __global__ void omega_to_t_fft_kernel(int n, int logn, long long plane, double d
     const int i = idx / kCols, c = idx % kCols;
     const int ri = logn ? int(__brev(unsigned(i)) >> (32 - logn)) : 0;
     double2 v = make_double2(0.0, 0.0);
-    if (c < cols) {
-      const float2 f = eh[(long long)i * plane + x0 + c];
+    const int li = i - first;
+    if (c < cols && li >= 0 && li < n_local) {
+      const float2 f = eh[(long long)li * plane + x0 + c];
       v = make_double2(double(f.x), double(f.y));
     }
     sm[ri * kCols + c] = v;
@@ -321,19 +325,22 @@ __global__ void omega_to_t_fft_kernel(int n, int logn, long long plane, double d
   }
 }
 
-// Direct FP64 sum for any n (used when n is not a power of two).
-__global__ void omega_to_t_direct_kernel(int n, long long plane, double domega,
-                                         const float2* __restrict__ eh, double2* out) {
+// Direct FP64 sum for any n (used when n is not a power of two), over this
+// plan's channels first .. first + n_local - 1 of the n.
+__global__ void omega_to_t_direct_kernel(int n, int first, int n_local, long long plane,
+                                         double domega, const float2* __restrict__ eh,
+                                         double2* out) {
   const long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
   if (x >= plane) return;
   const int ic = n / 2;
   double re = 0.0, im = 0.0;
-  for (int i = 0; i < n; ++i) {
+  for (int li = 0; li < n_local; ++li) {
+    const int i = first + li;
     const long long e = (((long long)(i - ic) * j) % n + n) % n;
     double s, co;
     sincospi(-2.0 * double(e) / double(n), &s, &co);
-    const float2 f = eh[(long long)i * plane + x];
+    const float2 f = eh[(long long)li * plane + x];
     re += double(f.x) * co - double(f.y) * s;
     im += double(f.x) * s + double(f.y) * co;
   }
@@ -376,19 +383,22 @@ cudaError_t launch_incident(const SetupArgs& sa, const double* omega, const doub
   return cudaGetLastError();
 }
 
-cudaError_t launch_omega_to_t(int n_ch, long long plane, double domega, const float2* eh,
-                              double2* out, cudaStream_t s) {
-  const bool pow2 = n_ch > 0 && (n_ch & (n_ch - 1)) == 0;
-  const size_t smem = size_t(n_ch) * kCols * sizeof(double2) + size_t(n_ch / 2) * sizeof(double2);
-  if (pow2 && n_ch >= 2 && smem <= 200 * 1024) {
+cudaError_t launch_omega_to_t(int n_total, int first, int n_local, long long plane,
+                              double domega, const float2* eh, double2* out, cudaStream_t s) {
+  if (first < 0 || n_local < 0 || first + n_local > n_total) return cudaErrorInvalidValue;
+  const int n = n_total;
+  const bool pow2 = n > 0 && (n & (n - 1)) == 0;
+  const size_t smem = size_t(n) * kCols * sizeof(double2) + size_t(n / 2) * sizeof(double2);
+  if (pow2 && n >= 2 && smem <= 200 * 1024) {
     int logn = 0;
-    while ((1 << logn) < n_ch) ++logn;
+    while ((1 << logn) < n) ++logn;
     const long long blocks = (plane + kCols - 1) / kCols;
-    omega_to_t_fft_kernel<<<int(blocks), 256, smem, s>>>(n_ch, logn, plane, domega, eh, out);
+    omega_to_t_fft_kernel<<<int(blocks), 256, smem, s>>>(n, logn, first, n_local, plane, domega,
+                                                        eh, out);
     return cudaGetLastError();
   }
-  dim3 grid(unsigned((plane + 127) / 128), unsigned(n_ch));
-  omega_to_t_direct_kernel<<<grid, 128, 0, s>>>(n_ch, plane, domega, eh, out);
+  dim3 grid(unsigned((plane + 127) / 128), unsigned(n));
+  omega_to_t_direct_kernel<<<grid, 128, 0, s>>>(n, first, n_local, plane, domega, eh, out);
   return cudaGetLastError();
 }
 

@@ -108,6 +108,20 @@ BPM_API bpm_status bpm_set_crystal(bpm_plan plan, double chi0_re, double chi0_im
  * Defaults: tan_psi = 0, unbounded z.  Errors: INVALID_ARG, CUDA. */
 BPM_API bpm_status bpm_set_geometry(bpm_plan plan, double tan_psi, double z_begin, double z_end);
 
+/* A crystal of any shape (the Introduction offers the method for crystals of
+ * arbitrary shape; the reflection geometry follows from the boundaries, end of
+ * Section 2). mask holds nz * ny * nx bytes ([nz][ny][nx], ny = 1 in 2D, x
+ * fastest). A nonzero byte is a crystal cell at (x_j, y_r, z_n) = (j dx, r dy,
+ * n dz).
+ * The mask replaces the boundaries of bpm_set_crystal / bpm_set_geometry for
+ * Pi(x, y, z_n). The coupling step is applied only in crystal cells, and the
+ * deformation phase e^{i h u} only there. NULL returns to the boundaries.
+ * Ownership: the plan keeps its own device copy; mask may be freed after the
+ * call. on_device says whether mask is a device pointer.
+ * Call before or after bpm_set_crystal (the deformation factor is rebuilt).
+ * Errors: INVALID_ARG (null plan), CUDA (allocation or copy). */
+BPM_API bpm_status bpm_set_crystal_shape(bpm_plan plan, const unsigned char* mask, int on_device);
+
 /* Incident pulse (Section 3.1 beam, Eq. ref:tdp and the frequency decomposition
  * after it): omega[n_channels] angular frequencies (rad/s, uniformly spaced for
  * the time assembly), weight_re_im[2*n_channels] complex spectral amplitudes

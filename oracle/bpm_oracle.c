@@ -61,6 +61,10 @@ typedef struct {
    * thickness along x, and the crystal cut to z_begin <= z < z_end (Laue slab
    * when the x range is unbounded). */
   double tan_psi, z_begin, z_end;
+  /* An arbitrary crystal shape (Introduction: the method takes crystals of
+   * any shape): Pi(x_j, y_r, z_n) = mask[(n ny + r) nx + j] != 0, [nz][ny][nx]
+   * bytes, replacing the boundaries above; NULL keeps them. */
+  const uint8_t* mask;
 } orc_problem;
 
 /* ------------------------------------------------------------------------- */
@@ -269,11 +273,15 @@ int orc_channel(const orc_problem* p, double omega, double* out_scalars, cplx* c
   return 0;
 }
 
-/* Crystal mask Pi(x_j, z_n): x_j = j dx, z_n = n dz,                         */
+/* Crystal mask Pi(x_j, y_r, z_n): x_j = j dx, z_n = n dz,                    */
 /*   x_surface + z tan_psi <= x_j < x_surface + z tan_psi + thickness           */
-/*   and z_begin <= z_n < z_end.                                               */
+/*   and z_begin <= z_n < z_end, or the caller's mask when one is given.       */
 /* tan_psi = 0 and an unbounded z range give the symmetric-Bragg slab.          */
-static int inside(const orc_problem* p, int j, int n) {
+static int inside(const orc_problem* p, int j, int r, int n) {
+  if (p->mask) {
+    int ny = (p->dims == 3) ? p->ny : 1;
+    return p->mask[((size_t)n * ny + r) * p->nx + j] != 0;
+  }
   double x = (double)j * p->dx;
   double z = (double)n * p->dz;
   if (!(z >= p->z_begin && z < p->z_end)) return 0;
@@ -293,7 +301,7 @@ int orc_deformation(const orc_problem* p, const double* u, int z_index, cplx* c_
   for (int r = 0; r < ny; ++r)
     for (int j = 0; j < p->nx; ++j) {
       size_t idx = (size_t)r * p->nx + j;
-      int in = inside(p, j, z_index);
+      int in = inside(p, j, r, z_index);
       cplx cv = 0;
       if (in) {
         double uu = u ? u[((size_t)z_index * ny + r) * p->nx + j] : 0.0;

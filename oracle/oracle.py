@@ -68,6 +68,7 @@ class Problem(ctypes.Structure):
         ("theta_i", ctypes.c_double), ("x0", ctypes.c_double), ("w0", ctypes.c_double),
         ("zx", ctypes.c_double), ("zR", ctypes.c_double),
         ("tan_psi", ctypes.c_double), ("z_begin", ctypes.c_double), ("z_end", ctypes.c_double),
+        ("mask", ctypes.c_void_p),
     ]
 
 
@@ -108,9 +109,18 @@ def _check(rc: int, what: str):
 
 
 def problem(w) -> Problem:
-    """Build the C problem record from a workload-like object."""
+    """Build the C problem record from a workload-like object.  An optional
+    w.mask ([nz][ny][nx], nonzero = crystal) replaces the geometric crystal
+    boundaries; the record keeps its byte copy alive."""
     dims = int(w.dims)
-    return Problem(
+    mask = getattr(w, "mask", None)
+    mbytes = None
+    if mask is not None:
+        ny = int(w.ny) if dims == 3 else 1
+        mbytes = np.ascontiguousarray((np.asarray(mask) != 0).astype(np.uint8))
+        if mbytes.size != int(w.nz) * ny * int(w.nx):
+            raise ValueError("mask must hold nz * ny * nx cells")
+    rec = Problem(
         dims, int(w.nx), int(w.ny) if dims == 3 else 1, int(w.nz),
         float(w.dx), float(w.dy) if dims == 3 else 0.0, float(w.dz),
         complex(w.chi0).real, complex(w.chi0).imag,
@@ -121,7 +131,10 @@ def problem(w) -> Problem:
         float(w.theta_i), float(w.x0), float(w.w0), float(w.zx), float(w.zR),
         float(getattr(w, "tan_psi", 0.0)), float(getattr(w, "z_begin", -np.inf)),
         float(getattr(w, "z_end", np.inf)),
+        None if mbytes is None else mbytes.ctypes.data_as(ctypes.c_void_p),
     )
+    rec._mask_bytes = mbytes
+    return rec
 
 
 def _plane(w) -> int:

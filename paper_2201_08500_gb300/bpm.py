@@ -29,7 +29,8 @@ EXPORTS = ("bpm_plan_create", "bpm_set_crystal", "bpm_set_pulse", "bpm_set_field
            "bpm_noalloc_scratch_bytes", "bpm_noalloc_last_error", "bpm_set_stream",
            "bpm_set_geometry", "bpm_batch_set_max_blocks", "bpm_batch_pending",
            "bpm_batch_graph_kernels", "bpm_get_launch", "bpm_set_launch", "bpm_tune",
-           "bpm_tune_save", "bpm_tune_load", "bpm_tune_clear", "bpm_set_channel_shard")
+           "bpm_tune_save", "bpm_tune_load", "bpm_tune_clear", "bpm_set_channel_shard",
+           "bpm_set_crystal_shape")
 
 
 class BpmError(RuntimeError):
@@ -92,6 +93,7 @@ def load(path: str = LIB_PATH):
         "bpm_set_pulse": ([_P, _P, _P, _D, _D, _D, _D, _D], _I),
         "bpm_set_fields": ([_P, _P, _P, _I, _I], _I),
         "bpm_set_channel_shard": ([_P, _I, _I, _D], _I),
+        "bpm_set_crystal_shape": ([_P, _P, _I], _I),
         "bpm_run": ([_P, _I], _I),
         "bpm_sync": ([_P], _I),
         "bpm_set_stream": ([_P, _P], _I),
@@ -220,6 +222,24 @@ class Plan:
             1 if _is_device(u) else 0))
         if _is_device(u):
             self._keep = [u]
+
+    def set_crystal_shape(self, mask):
+        """A crystal of any shape: mask [nz][ny][nx] (2D: [nz][nx]), nonzero =
+        crystal cell, as a host array or a device tensor of one byte per cell;
+        None returns to the crystal's boundaries (bpm_set_crystal_shape)."""
+        if mask is None:
+            self._check(self._L.bpm_set_crystal_shape(self._h, None, 0))
+            return
+        cells = self.nz * self.plane
+        if _is_device(mask):
+            if mask.numel() != cells or mask.element_size() != 1 or not mask.is_contiguous():
+                raise ValueError("device mask must be a contiguous byte tensor of nz*ny*nx cells")
+            self._check(self._L.bpm_set_crystal_shape(self._h, _ptr(mask), 1))
+            return
+        m = np.ascontiguousarray((np.asarray(mask) != 0).astype(np.uint8))
+        if m.size != cells:
+            raise ValueError("mask must hold nz * ny * nx cells")
+        self._check(self._L.bpm_set_crystal_shape(self._h, _ptr(m), 0))
 
     def set_geometry(self, tan_psi=0.0, z_begin=-np.inf, z_end=np.inf):
         self._check(self._L.bpm_set_geometry(self._h, float(tan_psi), float(z_begin),
@@ -353,6 +373,8 @@ def plan_from_workload(w, stream=None, u=None) -> Plan:
     geo = (getattr(w, "tan_psi", 0.0), getattr(w, "z_begin", -np.inf), getattr(w, "z_end", np.inf))
     if geo != (0.0, -np.inf, np.inf):
         p.set_geometry(*geo)
+    if getattr(w, "mask", None) is not None:
+        p.set_crystal_shape(w.mask)
     p.set_crystal(w.chi0, w.chih, w.chihb, w.theta_B, w.lambda_B, w.x_surface, w.thickness,
                   u=w.u if u is None else u)
     p.set_pulse(w.omega, w.S, w.theta_i, w.x0, w.w0, w.zx, w.zR)

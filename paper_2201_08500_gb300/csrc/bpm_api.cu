@@ -258,6 +258,7 @@ struct bpm_plan_s {
   float2* twx3 = nullptr;        // 3D: x twiddles (thread order)
   float2* qy = nullptr;          // 3D: {qy^2, 1/g_y - 1} per y-spectrum position
   const double* u_dev = nullptr;  // displacement used by the deformation setup (may be null)
+  unsigned char* mask = nullptr;  // caller's crystal shape [nz][ny][nx] (plan-owned copy) or null
   size_t bytes = 0;               // device bytes owned by the plan
 
   int group = 1, blocks = 0;
@@ -308,7 +309,7 @@ void free_plan_buffers(bpm_plan p) {
   void* ptrs[] = {p->cfield, p->e0,      p->eh,    p->tables, p->coef,     p->twiddle,
                   p->rev,    p->gain,    p->omega, p->weight, p->inc_norm, p->refl,
                   p->trans,  p->eh_time, p->dflag, p->u_tmp,  p->gcorr,    p->twy,
-                  p->qy,     p->spec,    p->twx3,  p->twiddle_t, p->twiddle_p};
+                  p->qy,     p->spec,    p->twx3,  p->twiddle_t, p->twiddle_p, p->mask};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->ev0) cudaEventDestroy(p->ev0);
@@ -611,6 +612,27 @@ BPM_API bpm_status bpm_set_geometry(bpm_plan p, double tan_psi, double z_begin, 
   p->sa.z_begin = z_begin;
   p->sa.z_end = z_end;
   p->have_geometry = true;
+  if (p->have_crystal) BPM_CUDA(p, enqueue_crystal(p), "deformation kernel");
+  return BPM_OK;
+}
+
+BPM_API bpm_status bpm_set_crystal_shape(bpm_plan p, const unsigned char* mask, int on_device) {
+  if (!p) return fail(nullptr, BPM_ERR_INVALID_ARG, "null plan");
+  if (!mask) {
+    p->sa.mask = nullptr;  // back to the crystal's boundaries (the copy is kept for reuse)
+  } else {
+    const size_t cells = size_t(p->grid.nz) * p->plane;
+    if (!p->mask) {
+      BPM_CUDA(p, dalloc(&p->mask, cells), "alloc crystal mask");
+      p->bytes += cells;
+    }
+    BPM_CUDA(p, cudaMemcpyAsync(p->mask, mask, cells,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                p->stream),
+             "upload crystal mask");
+    if (!on_device) BPM_CUDA(p, cudaStreamSynchronize(p->stream), "upload crystal mask");
+    p->sa.mask = p->mask;
+  }
   if (p->have_crystal) BPM_CUDA(p, enqueue_crystal(p), "deformation kernel");
   return BPM_OK;
 }

@@ -67,6 +67,7 @@ struct SetupArgs {
   double tan_psi;            // entrance surface x = x_surface + z tan_psi (asymmetric cut)
   double z_begin, z_end;     // crystal only for z_begin <= z < z_end (Laue slab)
   double theta_i, x0, w0, zx, zR;
+  const unsigned char* mask;  // [nz][ny][nx] crystal cells (nonzero), replacing the bounds; or null
 };
 
 // One work-queue item: channels ch0 .. ch0 + G - 1 of plan `plan` (transform size n).

@@ -1,7 +1,8 @@
 // Per-plan setup kernels of the BPM (FP64 arithmetic, run once per crystal /
 // pulse) and the frequency-to-time assembly.
 //
-//  deformation_kernel : c(x, z) = Pi(x) exp(+i h u(x, z))            (Eq. Authier)
+//  deformation_kernel : c(x, z) = Pi(x, z) exp(+i h u(x, z))         (Eq. Authier);
+//                       Pi from the crystal's boundaries or a caller's mask
 //  tables_kernel      : tilted propagators p+- and coupling coefficients
 //                       (Eqs. fov4, fov11, fov12, Zassenhaus-like factor)
 //  incident_kernel    : A+ = S g(x, y) exp(i (k sin theta_i - h/2) x), A- = 0
@@ -95,7 +96,7 @@ __global__ void deformation_kernel(SetupArgs sa, const double* __restrict__ u, f
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const int j = int(i % sa.nx);
-    const bool in = in_crystal(sa, j, int(i / plane));
+    const bool in = sa.mask ? sa.mask[i] != 0 : in_crystal(sa, j, int(i / plane));
     float2 c = make_float2(0.f, 0.f);
     if (in) {
       const double ph = u ? sa.h * u[i] : 0.0;

@@ -66,6 +66,9 @@ class Workload:
     tan_psi: float = 0.0
     z_begin: float = -math.inf
     z_end: float = math.inf
+    # an arbitrary crystal shape: [nz][nx] (2D) or [nz][ny][nx] (3D), nonzero =
+    # crystal; replaces the boundaries above when given
+    mask: np.ndarray | None = None
 
     @property
     def n_ch(self) -> int:

@@ -597,3 +597,74 @@ def test_strain_gradient_interbranch_fraction():
     assert abs(lz - 0.2651023751753087) < 1e-12
     assert abs(trans / lz - 1.0) < 1.5e-3, trans
     assert abs(trans + refl - 1.0) < 1e-3, (trans, refl)
+
+
+# ----------------------------------------------------------------------------- crystal shapes
+def _slab_mask(w, ny=1):
+    """Pi of the geometric crystal, written out from its definition (x_j = j dx,
+    z_n = n dz, half-open intervals; entrance x_surface + z tan_psi)."""
+    m = np.zeros((w.nz, ny, w.nx), np.uint8)
+    for n in range(w.nz):
+        z = float(n) * w.dz
+        if not (w.z_begin <= z < w.z_end):
+            continue
+        shift = z * w.tan_psi
+        lo = w.x_surface + shift
+        hi = (w.x_surface + w.thickness) + shift
+        for j in range(w.nx):
+            x = float(j) * w.dx
+            m[n, :, j] = 1 if lo <= x < hi else 0
+    return m if ny > 1 else m[:, 0, :]
+
+
+def test_all_crystal_mask_is_the_per_mode_matrix_power():
+    """A caller's mask replaces the crystal boundaries: Pi = 1 everywhere on
+    top of a narrow slab gives the exact per-mode evolution of the unbounded
+    crystal, v <- C diag(p+, p-) v for every Fourier mode."""
+    w = make(nx=64, nz=37, x_surface=20e-6, thickness=3e-6, x0=20 * 0.5e-6, w0=6 * 0.5e-6,
+             chihb=complex(-3e-6, 1e-8))
+    w.mask = np.ones((w.nz, w.nx), np.uint8)
+    e0, eh, init = orc.run(w, n_threads=1)
+    ch = orc.channel(w, w.omega[0])
+    C = np.array([[ch["a"], ch["bp"]], [ch["bm"], ch["a"]]])
+    F0 = orc.dft(init[0], -1)
+    out0 = np.zeros(w.nx, complex)
+    outh = np.zeros(w.nx, complex)
+    for m in range(w.nx):
+        M = C @ np.diag([ch["pp"][m], ch["pm"][m]])
+        out0[m], outh[m] = np.linalg.matrix_power(M, w.nz) @ np.array([F0[m], 0.0])
+    scale = np.max(np.abs(init))
+    assert np.max(np.abs(e0[0] - orc.dft(out0, +1))) < 1e-12 * scale
+    assert np.max(np.abs(eh[0] - orc.dft(outh, +1))) < 1e-12 * scale
+    w.mask = None
+    g0, gh, _ = orc.run(w, n_threads=1)
+    assert np.max(np.abs(gh[0] - eh[0])) > 1e-3 * scale   # the narrow slab alone differs
+
+
+def test_slab_shaped_mask_reproduces_the_geometric_crystal():
+    """A mask drawn from the boundaries of an asymmetric cut in a z range
+    (x_j, z_n sampled as the boundaries are) gives the same fields, bit for bit;
+    with the mask the boundaries no longer matter."""
+    rng = np.random.default_rng(5)
+    w = make(nx=128, nz=40, x_surface=30 * 0.5e-6, thickness=40 * 0.5e-6, x0=12 * 0.5e-6,
+             w0=5 * 0.5e-6, tan_psi=0.3, z_begin=3 * 0.5e-6, z_end=31 * 0.5e-6,
+             u=rng.uniform(-2e-11, 2e-11, (40, 128)))
+    ref0, refh, _ = orc.run(w, n_threads=1)
+    m = _slab_mask(w)
+    assert 0 < m.sum() < m.size
+    g = make(nx=128, nz=40, x_surface=-1.0, thickness=0.0, x0=w.x0, w0=w.w0, u=w.u, mask=m)
+    e0, eh, _ = orc.run(g, n_threads=1)
+    assert np.array_equal(e0, ref0) and np.array_equal(eh, refh)
+
+
+def test_3d_slab_shaped_mask_reproduces_the_geometric_crystal():
+    """The same in 3D, mask [nz][ny][nx] (nx != ny, so a transposed index differs)."""
+    w = make(dims=3, nx=32, ny=16, nz=6, dx=1e-6, dy=1e-6, dz=0.25e-6, x_surface=10e-6,
+             thickness=12e-6, x0=6e-6, w0=3e-6, tan_psi=0.5)
+    ref0, refh, _ = orc.run(w, n_threads=1)
+    m = _slab_mask(w, ny=16)
+    g = make(dims=3, nx=32, ny=16, nz=6, dx=1e-6, dy=1e-6, dz=0.25e-6, x_surface=-1.0,
+             thickness=0.0, x0=6e-6, w0=3e-6, mask=m)
+    e0, eh, _ = orc.run(g, n_threads=1)
+    assert np.array_equal(e0, ref0) and np.array_equal(eh, refh)
+    assert np.any(refh)

@@ -310,8 +310,8 @@ typedef struct bpm_batch_s* bpm_batch;
  * Errors: INVALID_ARG, CUDA. */
 BPM_API bpm_status bpm_batch_create(size_t hbm_budget_bytes, void* cuda_stream, bpm_batch* out);
 
-/* Admits a plan whose crystal and pulse are set; it is marched from its current
- * z to nz by later rounds.  Until its ticket completes (or is cancelled) the
+/* Admits a 2D plan whose crystal and pulse are set, of any splitting order (1,
+ * 2 or 4); it is marched from its current z to nz by later rounds.  Until its ticket completes (or is cancelled) the
  * plan works on the batch stream (its pending work is ordered before the
  * batch); then its original stream is restored.  The caller keeps ownership
  * and destroys the plan after its ticket reports done (or after cancel).

@@ -1333,8 +1333,6 @@ BPM_API bpm_status bpm_batch_submit(bpm_batch b, bpm_plan p, uint64_t* ticket) {
   if (!b || !p || !ticket) return bfail(b, BPM_ERR_INVALID_ARG, "null argument");
   if (!p->have_pulse) return bfail(b, BPM_ERR_STATE, "plan needs crystal and pulse first");
   if (p->grid.dims != 2) return bfail(b, BPM_ERR_UNSUPPORTED, "batches take 2D plans");
-  if (p->grid.split_order == 4)
-    return bfail(b, BPM_ERR_UNSUPPORTED, "batches take split orders 1 and 2");
   for (const auto& e : b->entries)
     if (e.plan == p) return bfail(b, BPM_ERR_STATE, "plan already in the batch");
   if (b->budget && b->used + p->bytes > b->budget)

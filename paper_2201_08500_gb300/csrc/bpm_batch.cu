@@ -8,7 +8,9 @@
 // 4, 2, 1 channels into the 256-thread block, each with its own shared-memory
 // slot (at most 196 KB).  Nx = 8192 needs 512 threads and runs in a sibling
 // kernel of the same structure, with the parked-envelope body (bpm_parked.cuh).
-// First-order items at Nx >= 2048 run in the tensor-memory kernels below.  The counter lives in global memory and is
+// First-order items at Nx >= 2048 run in the tensor-memory kernels below;
+// second- and fourth-order items in their own instantiations of the two
+// kernels above (one queue per order and size class).  The counter lives in global memory and is
 // cleared before each launch; the queue never waits, so no block can hang.
 #include <cuda_runtime.h>
 
@@ -31,8 +33,15 @@ constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
 constexpr size_t kSmallSmem =
     cmax(cmax(cmax(item_smem<256>(), item_smem<512>()), cmax(item_smem<1024>(), item_smem<2048>())),
          item_smem<4096>());
+static_assert(Resident<4096, 1, 4>::smem_bytes() <= kSmallSmem &&
+                  Resident<256, 16, 4>::smem_bytes() <= kSmallSmem &&
+                  Resident<256, 16, 2>::smem_bytes() <= kSmallSmem,
+              "every order's resident slot fits the first-order bound");
 
-template <bool STRANG>
+// SPLIT: Eq. split-op order of the queue's plans (1, 2 or 4).  The resident
+// body keeps its tables in shared memory only at first and second order, so
+// kSmallSmem (first order) bounds every order.
+template <int SPLIT>
 __global__ void __launch_bounds__(kSmallThreads, 1)
     batch_kernel(const MarchArgs* __restrict__ plans, const BatchItem* __restrict__ items,
                  int n_items, int* counter) {
@@ -47,17 +56,17 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
     const BatchItem item = items[it];
     const MarchArgs& A = plans[item.plan];
     switch (item.n) {
-      case 256: Resident<256, 16, STRANG ? 2 : 1>::run_item(A, item.ch0, smem); break;
-      case 512: Resident<512, 8, STRANG ? 2 : 1>::run_item(A, item.ch0, smem); break;
-      case 1024: Resident<1024, 4, STRANG ? 2 : 1>::run_item(A, item.ch0, smem); break;
-      case 2048: Resident<2048, 2, STRANG ? 2 : 1>::run_item(A, item.ch0, smem); break;
-      case 4096: Resident<4096, 1, STRANG ? 2 : 1>::run_item(A, item.ch0, smem); break;
+      case 256: Resident<256, 16, SPLIT>::run_item(A, item.ch0, smem); break;
+      case 512: Resident<512, 8, SPLIT>::run_item(A, item.ch0, smem); break;
+      case 1024: Resident<1024, 4, SPLIT>::run_item(A, item.ch0, smem); break;
+      case 2048: Resident<2048, 2, SPLIT>::run_item(A, item.ch0, smem); break;
+      case 4096: Resident<4096, 1, SPLIT>::run_item(A, item.ch0, smem); break;
       default: break;
     }
   }
 }
 
-template <bool STRANG>
+template <int SPLIT>
 __global__ void __launch_bounds__(512, 1)
     batch_kernel_8192(const MarchArgs* __restrict__ plans, const BatchItem* __restrict__ items,
                       int n_items, int* counter) {
@@ -70,7 +79,7 @@ __global__ void __launch_bounds__(512, 1)
     const int it = s_item;
     if (it >= n_items) break;
     const BatchItem item = items[it];
-    if (item.n == 8192) Parked<8192, STRANG ? 2 : 1>::run_item(plans[item.plan], item.ch0, smem);
+    if (item.n == 8192) Parked<8192, SPLIT>::run_item(plans[item.plan], item.ch0, smem);
   }
 }
 
@@ -118,6 +127,7 @@ int batch_queue(int n, int split_order) {
     if (n == 2048) return kQueueTm2048;
     return kQueueSmall;
   }
+  if (split_order == 4) return n == 8192 ? kQueueBig4 : kQueueSmall4;
   return n == 8192 ? kQueueBig2 : kQueueSmall2;
 }
 
@@ -147,13 +157,19 @@ cudaError_t launch_batch(const MarchArgs* plans, const BatchItem* items, int n_i
           plans, items, n_items, counter);
       break;
     case kQueueSmall:
-      batch_kernel<false><<<blocks, kSmallThreads, kSmallSmem, s>>>(plans, items, n_items, counter);
+      batch_kernel<1><<<blocks, kSmallThreads, kSmallSmem, s>>>(plans, items, n_items, counter);
       break;
     case kQueueBig2:
-      batch_kernel_8192<true><<<blocks, 512, big_smem, s>>>(plans, items, n_items, counter);
+      batch_kernel_8192<2><<<blocks, 512, big_smem, s>>>(plans, items, n_items, counter);
       break;
     case kQueueSmall2:
-      batch_kernel<true><<<blocks, kSmallThreads, kSmallSmem, s>>>(plans, items, n_items, counter);
+      batch_kernel<2><<<blocks, kSmallThreads, kSmallSmem, s>>>(plans, items, n_items, counter);
+      break;
+    case kQueueBig4:
+      batch_kernel_8192<4><<<blocks, 512, big_smem, s>>>(plans, items, n_items, counter);
+      break;
+    case kQueueSmall4:
+      batch_kernel<4><<<blocks, kSmallThreads, kSmallSmem, s>>>(plans, items, n_items, counter);
       break;
     default:
       return cudaErrorInvalidValue;
@@ -165,9 +181,11 @@ cudaError_t batch_set_attributes() {
   const int small = int(kSmallSmem), big = int(Parked<8192, 1>::smem_bytes());
   const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t r[] = {
-      cudaFuncSetAttribute(batch_kernel<false>, attr, small),
-      cudaFuncSetAttribute(batch_kernel<true>, attr, small),
-      cudaFuncSetAttribute(batch_kernel_8192<true>, attr, big),
+      cudaFuncSetAttribute(batch_kernel<1>, attr, small),
+      cudaFuncSetAttribute(batch_kernel<2>, attr, small),
+      cudaFuncSetAttribute(batch_kernel<4>, attr, small),
+      cudaFuncSetAttribute(batch_kernel_8192<2>, attr, big),
+      cudaFuncSetAttribute(batch_kernel_8192<4>, attr, big),
       cudaFuncSetAttribute(batch_kernel_tm<8192>, attr, int(Parked<8192, 1, true, false>::smem_bytes())),
       cudaFuncSetAttribute(batch_kernel_tm<4096>, attr, int(Parked<4096, 1, true, false>::smem_bytes())),
       cudaFuncSetAttribute(batch_kernel_tm<2048>, attr, int(Parked<2048, 1, true, false>::smem_bytes()))};

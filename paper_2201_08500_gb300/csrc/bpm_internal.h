@@ -87,6 +87,8 @@ enum BatchQueue {
   kQueueTm2048,      // first order, Nx = 2048: parked form, TMEM tables, 4 blocks / SM
   kQueueSmall,       // first order, Nx <= 1024: resident form, G channels per block
   kQueueSmall2,      // Strang, Nx <= 4096: resident form
+  kQueueBig4,        // fourth order, Nx = 8192: parked form, L2 tables (two sets)
+  kQueueSmall4,      // fourth order, Nx <= 4096: resident form, L2 tables (two sets)
   kQueueCount
 };
 int batch_group(int n);                               // channels per block of the resident kernels

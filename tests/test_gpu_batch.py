@@ -191,6 +191,35 @@ def test_strang_plans_in_a_mixed_batch(stream):
     b.close()
 
 
+def test_fourth_order_plans_in_a_mixed_batch(stream):
+    """Fourth-order plans (Eq. split-op, t = 1/(2 - 2^(1/3))) at Nx = 1024, 8192
+    and 256 share the batch with first- and second-order plans: each equals its
+    single-plan march bitwise, and the oracle on sampled channels."""
+    ws = mix(seed=23)
+    for i in (0, 3, 5):
+        ws[i].split_order = 4
+    ws[1].split_order = 2
+    ref = [single(w, stream) for w in ws]
+    b = bpm.Batch(stream=stream)
+    plans = [bpm.plan_from_workload(w, stream=stream) for w in ws]
+    for p in plans:
+        b.submit(p)
+    b.run()
+    b.sync()
+    for p, r in zip(plans, ref):
+        assert_same(fetch(p), r)
+        p.close()
+    b.close()
+    for i in (0, 3):
+        w, r = ws[i], ref[i]
+        pick = [0, w.n_ch - 1]
+        o0, oh, init = orc.run(w.subset(pick))
+        inc = np.linalg.norm(init, axis=1)
+        err = max(np.max(np.linalg.norm(r["e0"][pick] - o0, axis=1) / inc),
+                  np.max(np.linalg.norm(r["eh"][pick] - oh, axis=1) / inc))
+        assert err < TOL_FIELD, (w.name, err)
+
+
 def test_block_cap_and_rounds_in_flight(stream):
     """A batch capped at 3 blocks gives the same fields; pending() counts rounds
     whose kernels have not finished and is 0 after a sync."""

@@ -236,9 +236,9 @@ def test_fourth_order_splitting_matches_oracle(stream, nx):
     assert np.linalg.norm(g2["eh"] - g["eh"]) > 1e-5 * np.linalg.norm(g["eh"])  # a different scheme
 
 
-def test_fourth_order_grouped_channels_and_batch_refusal(stream):
-    """Several channels per block at N = 512 with a ragged tail; batches refuse
-    fourth-order plans."""
+def test_fourth_order_grouped_channels(stream):
+    """Several channels per block at N = 512 with a ragged tail (fourth-order
+    plans in batches: test_gpu_batch.py)."""
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     w = deformed_small(512, nz=30, n_ch=8 * sms + 5, seed=12)
@@ -250,10 +250,6 @@ def test_fourth_order_grouped_channels_and_batch_refusal(stream):
     g = dict(e0=p.e0(), eh=p.eh())
     e = errors(w, g, channels=[0, 7, 8, w.n_ch - 1])
     assert e["per_ch"] < TOL_FIELD, e
-    b = bpm.Batch(stream=stream)
-    with pytest.raises(bpm.BpmError):
-        b.submit(p)
-    b.close()
     p.close()
 
 

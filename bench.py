@@ -43,6 +43,12 @@ METRIC = "BPM cell-updates/s (omega*x*z)"
 # rows are re-read by each wave of channels, which at ~9 GB/s is immaterial to
 # this ALU-bound kernel.  Keyed by kernel, form and workload; any other
 # configuration reports null.
+# DRAM bytes of one z step of the 3D workload (one column pass + one MODE-1 row
+# pass, 256-thread row tile), from the live launch list of those launches with
+# --cache-control none: 1239 + 1085 MB.  Algorithmic: 64 B per cell-update =
+# 2147 MB; the excess is the row pass's output draining from L2 during the
+# column pass.
+MEASURED_TRAFFIC_3D = {("large-3d-512x512-nz1000-ch128", 0, 256): 2323.87e6}
 MEASURED_TRAFFIC = {
     ("march_kernel<4096,1> form 0", "deformed-2d-nx4096-nz2000-ch1024", 1): 660.43e6,
     ("march_kernel<4096,1> form 3", "deformed-2d-nx4096-nz2000-ch1024", 1): 589.01e6,
@@ -336,7 +342,11 @@ def run_3d(args, world, rank, local):
                    "l2": "fields (512 MB) exceed L2 (129 MB)", "launch": plan.launch(),
                    "tuned": tried},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": MEASURED_TRAFFIC_3D.get(
+                         (w.name, plan.launch()["form"], plan.launch()["row_threads"])),
+                     "traffic_unit": "one z step: column pass + row pass",
+                     "algorithmic_bytes": 64 * w.n_ch * w.plane,
                      "kernel": "row_pass_kernel + col_pass_kernel (2 passes per z step)",
                      "bytes_per_cell_update": 64, "march_ms": march_ms,
                      "passes": st["march_launches"]},

@@ -19,13 +19,17 @@
 // the padded exchange size) and the reduction area: 209.4 KB at 8192.  Tables
 // and stage twiddles are read from L2 (or TMEM).
 //
-// Barriers: an envelope's transform alternates its exchanges between the park
-// area that is free while it runs and the exchange buffer (park, buffer, park,
-// buffer).  Each exchange then needs one block barrier (between its stores and
-// its loads) instead of two: the barrier of exchange i + 1 already orders every
-// thread's loads of exchange i before anyone stores into that buffer again at
-// exchange i + 2.  A step adds one barrier at its start and one between the
-// parking and the second transform, 10 barriers instead of 16.
+// Barriers.  After the first radix-16 stage the transform splits into
+// independent sub-transforms of L(1) = N/16 positions, each held by LN(1) =
+// N/256 <= 32 threads of one warp in the layouts of stages 1 and 2, so the two
+// middle exchanges (stage 1 -> 2 and back) are warp-local and synchronise with
+// __syncwarp; only the first and the last exchange of a transform are
+// block-wide.  The middle exchanges use the park area that is free while the
+// envelope is in registers, the outer ones the exchange buffer: the first
+// needs one block barrier (between its stores and its loads), the last two
+// (its stores must wait for every warp's loads of the first).  A step adds one
+// barrier at its start and one between the parking and the second transform:
+// 8 block barriers a step.
 //
 // States of a step: [E0 in v, Eh parked] -> propagate E0 -> park E0, take Eh
 // -> propagate Eh -> [Eh in v, E0 parked] -> couple (reading E0 back) ->
@@ -132,15 +136,20 @@ struct Parked {
   }
 
   // Single-envelope exchange through the padded layout (Pad<N>, 64-bit slots).
-  // No leading barrier: no thread may still be reading x (see propagate).
-  template <int SF, int ST>
+  // WARP: the exchange moves data within each warp (the middle stages), so a
+  // warp barrier orders it; LEAD: a leading barrier of that scope first (see
+  // propagate for which exchange needs one).
+  template <int SF, int ST, bool WARP, bool LEAD>
   static BPM_DEV void exchange(float2 (&v)[16], float2* x, int t) {
     using P = Pad<N>;
     float2* st = x + P::template base<SF>(t);
     const float2* ld = x + P::template base<ST>(t);
+    if constexpr (LEAD) {
+      if constexpr (WARP) __syncwarp(); else __syncthreads();
+    }
 #pragma unroll
     for (int k = 0; k < 16; ++k) st[P::template off<SF>(k)] = v[k];
-    __syncthreads();
+    if constexpr (WARP) __syncwarp(); else __syncthreads();
 #pragma unroll
     for (int k = 0; k < 16; ++k) v[k] = ld[P::template off<ST>(k)];
   }
@@ -187,16 +196,19 @@ struct Parked {
     }
   }
 
-  // The four exchanges alternate xa, xb, xa, xb.  On entry no thread may still
-  // be reading xa or have reads of xb pending behind the first exchange's
-  // barrier; on return xa is free and other threads may still load from xb.
+  // Exchanges: block-wide through xa, warp-local through xb (twice), then
+  // block-wide through xa after a leading barrier.  On entry no thread may
+  // still be reading xa, and every read of xb must come before the first
+  // exchange's barrier; on return xb is free and other threads may still load
+  // from xa.
   static BPM_DEV void propagate(float2 (&v)[16], float2* xa, float2* xb, const float4* gt,
                                 uint32_t tcol, const float4* tw, int t) {
     static_assert(S == 3 || (S == 4 && kPairLast), "parked form: 1024 <= N <= 8192, 4 exchanges");
+    static_assert(Gm::LN(1) <= 32, "stage-1 sub-transforms within one warp");
     stage_fwd<0>(v, tw, t);
-    exchange<0, 1>(v, xa, t);
+    exchange<0, 1, false, false>(v, xa, t);
     stage_fwd<1>(v, tw, t);
-    exchange<1, 2>(v, xb, t);
+    exchange<1, 2, true, false>(v, xb, t);
     stage_fwd<2>(v, tw, t);
     if constexpr (kPairLast) {
       pair_swap(v, t);
@@ -219,9 +231,9 @@ struct Parked {
       multiply(v, gt, tcol, t);
     }
     stage_inv<2>(v, tw, t);
-    exchange<2, 1>(v, xa, t);
+    exchange<2, 1, true, true>(v, xb, t);
     stage_inv<1>(v, tw, t);
-    exchange<1, 0>(v, xb, t);
+    exchange<1, 0, false, true>(v, xa, t);
     stage_inv<0>(v, tw, t);
   }
 
@@ -271,11 +283,11 @@ struct Parked {
   static BPM_DEV void propagate_both(float2 (&v)[16], float2* x, float2* p0, float2* ph,
                                      const float4* gt, uint32_t tcol, const float4* tw, int t) {
     __syncthreads();  // own-slot accesses of p0 / ph and loads of x are done
-    propagate(v, p0, x, gt, tcol, tw, t);  // p0 is free while E0 is in registers
+    propagate(v, x, p0, gt, tcol, tw, t);  // p0 is free while E0 is in registers
     park(v, p0, t);
     unpark(v, ph, t);
     __syncthreads();  // x loads and the unparking of ph are done
-    propagate(v, ph, x, gt + N, tcol + 64u, tw, t);
+    propagate(v, x, ph, gt + N, tcol + 64u, tw, t);
   }
 
   // [Eh in v, E0 parked] -> coupling at z_n -> [E0 in v, Eh parked].

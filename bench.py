@@ -416,7 +416,10 @@ def run_served(args, world, rank, local):
         return st
 
     served = make()
+    sampler = ClockSampler(local)  # clocks during the served (headline) run
+    sampler.start()
     s_stats = served_form(served, 4)
+    clocks = sampler.stop()
     one = make()
     o_stats = served_form(one, 0)
     plain = make()
@@ -445,6 +448,7 @@ def run_served(args, world, rank, local):
         "burst": {"served": sb_stats, "plain": pb_stats,
                   "served_vs_plain_throughput": sb_stats["throughput"] / pb_stats["throughput"]},
         "results_equal_alone_vs_mix": same,
+        "clocks": clocks,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -229,8 +229,9 @@ BPM_API bpm_status bpm_get_stats(bpm_plan plan, bpm_stats* out);
  *                      Nx <= 4096, channels_per_block = the size's maximum);
  *                      2 = parked: one envelope in registers, the other in
  *                      shared memory, tables and twiddles from L2, one channel
- *                      per block and 512/(Nx/16) blocks per SM (first order,
- *                      Nx = 1024, 2048, 4096, channels_per_block = 1);
+ *                      per block and 512/(Nx/16) blocks per SM (first or
+ *                      fourth order, Nx = 1024, 2048, 4096,
+ *                      channels_per_block = 1);
  *                      3 = parked with the tables in tensor memory (TMEM)
  *                      instead of L2 (first order or Strang, Nx = 2048, 4096,
  *                      8192, channels_per_block = 1).

@@ -339,7 +339,9 @@ bool launch_valid(const bpm_grid& g, int form, int group, int row_threads) {
   if (row_threads != 256) return false;
   if (form == 0) return group == 1 || group == maxg;
   if (form == 2 || form == 3)
-    return group == 1 && (g.split_order == 1 || (form == 3 && g.split_order == 2)) &&
+    return group == 1 &&
+           (g.split_order == 1 || (form == 3 && g.split_order == 2) ||
+            (form == 2 && g.split_order == 4)) &&
            march_parked_supported(g.nx, form);
   return form == 1 && g.split_order == 1 && march_l2_supported(g.nx, group);
 }
@@ -751,7 +753,7 @@ BPM_API bpm_status bpm_run(bpm_plan p, int n_steps) {
   if (p->grid.dims == 2) {
     if (p->form == 1 && a.split_order == 1)
       BPM_CUDA(p, launch_march_l2(p->grid.nx, p->group, p->blocks, a, p->stream), "march kernel");
-    else if ((p->form == 2 && a.split_order == 1) || (p->form == 3 && a.split_order <= 2))
+    else if ((p->form == 2 && a.split_order != 2) || (p->form == 3 && a.split_order <= 2))
       BPM_CUDA(p, launch_march_parked(p->grid.nx, p->form, p->blocks, a, p->stream),
                "march kernel");
     else

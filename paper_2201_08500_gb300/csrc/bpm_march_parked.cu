@@ -1,9 +1,10 @@
 // First-order resident march, parked forms (Parked<N>: one envelope in
 // registers, the other in shared memory, at most 128 registers): one channel
 // per block of N/16 threads and 512/(N/16) blocks per SM, each at its own FFT
-// phase.  Form 2 (Nx = 1024, 2048, 4096) reads the tables from L2; form 3
-// (Nx = 2048, 4096, 8192) keeps them in tensor memory, first order or Strang.  Same per-channel
-// arithmetic as the other forms (bitwise the same fields).
+// phase.  Form 2 (Nx = 1024, 2048, 4096, first or fourth order) reads the
+// tables from L2; form 3 (Nx = 2048, 4096, 8192, first order or Strang) keeps
+// them in tensor memory.  Same per-channel arithmetic as the other forms
+// (bitwise the same fields).
 #include <cuda_runtime.h>
 
 #include "bpm_march_impl.cuh"
@@ -29,7 +30,8 @@ cudaError_t march_set_attributes_parked() {
                      attr_one<4096, 1, 1, 2>(), attr_one<2048, 1, 1, 3>(),
                      attr_one<4096, 1, 1, 3>(), attr_one<8192, 1, 1, 3>(),
                      attr_one<2048, 1, 2, 3>(), attr_one<4096, 1, 2, 3>(),
-                     attr_one<8192, 1, 2, 3>()};
+                     attr_one<8192, 1, 2, 3>(), attr_one<1024, 1, 4, 2>(),
+                     attr_one<2048, 1, 4, 2>(), attr_one<4096, 1, 4, 2>()};
   for (cudaError_t x : r)
     if (x != cudaSuccess) e = x;
   return e;
@@ -40,6 +42,12 @@ cudaError_t launch_march_parked(int n, int form, int blocks, const MarchArgs& a,
     if (n == 2048) return launch_one<2048, 1, 2, 3>(blocks, a, s);
     if (n == 4096) return launch_one<4096, 1, 2, 3>(blocks, a, s);
     if (n == 8192) return launch_one<8192, 1, 2, 3>(blocks, a, s);
+    return cudaErrorInvalidValue;
+  }
+  if (form == 2 && a.split_order == 4) {  // fourth order: two table sets from L2
+    if (n == 1024) return launch_one<1024, 1, 4, 2>(blocks, a, s);
+    if (n == 2048) return launch_one<2048, 1, 4, 2>(blocks, a, s);
+    if (n == 4096) return launch_one<4096, 1, 4, 2>(blocks, a, s);
     return cudaErrorInvalidValue;
   }
   if (a.split_order != 1) return cudaErrorInvalidValue;

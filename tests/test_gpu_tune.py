@@ -66,6 +66,19 @@ def test_strang_tmem_form_gives_identical_fields(nx):
         assert np.array_equal(got[k], ref[k]), k
 
 
+@pytest.mark.parametrize("nx", [1024, 4096])
+def test_fourth_order_parked_form_gives_identical_fields(nx):
+    """Fourth-order splitting in the parked form (tables from L2, two sets)
+    equals the resident form."""
+    w = deformed_small(nx, nz=24, n_ch=5, seed=33)
+    w.split_order = 4
+    ref, _ = fields(w, form=0, channels_per_block=1)
+    got, used = fields(w, form=2, channels_per_block=1)
+    assert used["form"] == 2
+    for k in ("e0", "eh", "R"):
+        assert np.array_equal(got[k], ref[k]), k
+
+
 def test_3d_row_tiles_give_identical_fields():
     from test_gpu_3d import case3d
     w = case3d(512, 256, 16, 2, seed=5)

@@ -204,7 +204,10 @@ BPM_API bpm_status bpm_fetch_reflectivity(bpm_plan plan, double* R, double* T, d
 /* Timing and launch accounting of the most recent bpm_run (after bpm_sync):
  * march_ms is the device time of the march kernel(s) measured with CUDA events
  * on the plan's stream (0 unless enabled with bpm_set_timing), launches is the
- * number of kernels bpm_run enqueued. */
+ * number of kernels bpm_run enqueued.  The paper has no counterpart.
+ * bpm_set_timing errors: INVALID_ARG (null plan), CUDA (event creation).
+ * bpm_get_stats errors: INVALID_ARG (null argument), STATE (the run has not
+ * finished: call bpm_sync first), CUDA. */
 typedef struct {
   double march_ms;
   int32_t launches;
@@ -352,7 +355,8 @@ BPM_API bpm_status bpm_batch_poll(bpm_batch b, uint64_t ticket, int* done);
  * enqueued).  Errors: STATE (already finishing), INVALID_ARG. */
 BPM_API bpm_status bpm_batch_cancel(bpm_batch b, uint64_t ticket);
 
-/* Waits for all enqueued rounds. */
+/* Waits for all enqueued rounds.  Errors: INVALID_ARG (null batch), CUDA (a
+ * round's kernels failed). */
 BPM_API bpm_status bpm_batch_sync(bpm_batch b);
 
 /* Number of enqueued rounds whose kernels have not finished (0..3).  A step

@@ -360,7 +360,7 @@ BPM_API bpm_status bpm_batch_cancel(bpm_batch b, uint64_t ticket);
 BPM_API bpm_status bpm_batch_sync(bpm_batch b);
 
 /* Number of enqueued rounds whose kernels have not finished (0..3).  A step
- * while 3 rounds are in flight waits for the oldest on the host; a driver that
+ * while 3 rounds are in flight waits for the oldest on the host; a caller that
  * must not block (a server feeding several batches) steps only below 3.
  * Errors: INVALID_ARG, CUDA (a round's kernels failed). */
 BPM_API bpm_status bpm_batch_pending(bpm_batch b, int* rounds_in_flight);

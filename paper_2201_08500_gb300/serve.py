@@ -1,4 +1,4 @@
-"""Continuous-batching BPM server on one GPU (driver of the C++ batch executor).
+"""Continuous-batching BPM server on one GPU (the host loop over the C++ batch executor).
 
 Requests are workload records (one crystal + pulse each) with arrival times.
 The served form:

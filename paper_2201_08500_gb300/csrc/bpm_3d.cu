@@ -135,12 +135,12 @@ struct Fft2Env {
   template <int s>
   static BPM_DEV void sfwd(float2 (&a)[16], float2 (&b)[16], const float2* tw, int t) {
     if constexpr (s < S - 1) {
-      dft16_fwd(a);
-      dft16_fwd(b);
+      dft16_fwd<false>(a);
+      dft16_fwd<false>(b);
       twid<s>(a, b, tw, t, false);
     } else {
-      last_stage<Gm::RLAST, false>(a);
-      last_stage<Gm::RLAST, false>(b);
+      last_stage<Gm::RLAST, false, false>(a);
+      last_stage<Gm::RLAST, false, false>(b);
     }
   }
 
@@ -148,11 +148,11 @@ struct Fft2Env {
   static BPM_DEV void sinv(float2 (&a)[16], float2 (&b)[16], const float2* tw, int t) {
     if constexpr (s < S - 1) {
       twid<s>(a, b, tw, t, true);
-      dft16_inv(a);
-      dft16_inv(b);
+      dft16_inv<false>(a);
+      dft16_inv<false>(b);
     } else {
-      last_stage<Gm::RLAST, true>(a);
-      last_stage<Gm::RLAST, true>(b);
+      last_stage<Gm::RLAST, true, false>(a);
+      last_stage<Gm::RLAST, true, false>(b);
     }
   }
 

@@ -143,24 +143,94 @@ BPM_DEV float2 w16(float2 z) {
   }
 }
 
+// The W16^2 and W16^6 rotations are c8 (x +- y, y -+ x): the +-1 combination
+// P_E(z) below, scaled by c8.  Where such a rotated value enters a 4-point
+// butterfly, the c8 product goes into the butterfly's additions as an FMA
+// (dft4_c, dft4_bd) instead of being rounded on its own: the same FP32
+// constants, two to four fewer instructions per butterfly.
+template <int E, bool INV>
+BPM_DEV float2 pre8(float2 z) {
+  static_assert(E == 2 || E == 6, "W8 rotations");
+  const float x = z.x, y = z.y;
+  if constexpr (!INV) {
+    return E == 2 ? make_float2(x + y, y - x) : make_float2(y - x, -x - y);
+  } else {
+    return E == 2 ? make_float2(x - y, x + y) : make_float2(-x - y, x - y);
+  }
+}
+
+// Outputs of a 4-point DFT from s0 = a + c, d0 = a - c, s1 = b + d, d1 = b - d.
+template <bool INV>
+BPM_DEV void dft4_out(float2 s0, float2 d0, float2 s1, float2 d1, float2& a, float2& b, float2& c,
+                      float2& d) {
+  a = c_add(s0, s1);
+  c = c_sub(s0, s1);
+  if (!INV) {
+    b = make_float2(d0.x + d1.y, d0.y - d1.x);
+    d = make_float2(d0.x - d1.y, d0.y + d1.x);
+  } else {
+    b = make_float2(d0.x - d1.y, d0.y + d1.x);
+    d = make_float2(d0.x + d1.y, d0.y - d1.x);
+  }
+}
+
+// dft4 whose input c still owes the rotation W16^E (E = 2 or 6).
+template <int E, bool INV>
+BPM_DEV void dft4_c(float2& a, float2& b, float2& c, float2& d) {
+  const float2 p = pre8<E, INV>(c);
+  const float2 s0 = make_float2(fmaf(p.x, BPM_C8, a.x), fmaf(p.y, BPM_C8, a.y));
+  const float2 d0 = make_float2(fmaf(-p.x, BPM_C8, a.x), fmaf(-p.y, BPM_C8, a.y));
+  dft4_out<INV>(s0, d0, c_add(b, d), c_sub(b, d), a, b, c, d);
+}
+
+// dft4 whose input b still owes W16^2 and d still owes W16^6.
+template <bool INV>
+BPM_DEV void dft4_bd(float2& a, float2& b, float2& c, float2& d) {
+  const float2 pb = pre8<2, INV>(b), pd = pre8<6, INV>(d);
+  const float2 P = c_add(pb, pd), Q = c_sub(pb, pd);  // s1 = c8 P, d1 = c8 Q
+  const float2 s0 = c_add(a, c), d0 = c_sub(a, c);
+  a = make_float2(fmaf(P.x, BPM_C8, s0.x), fmaf(P.y, BPM_C8, s0.y));
+  c = make_float2(fmaf(-P.x, BPM_C8, s0.x), fmaf(-P.y, BPM_C8, s0.y));
+  if (!INV) {
+    b = make_float2(fmaf(Q.y, BPM_C8, d0.x), fmaf(-Q.x, BPM_C8, d0.y));
+    d = make_float2(fmaf(-Q.y, BPM_C8, d0.x), fmaf(Q.x, BPM_C8, d0.y));
+  } else {
+    b = make_float2(fmaf(-Q.y, BPM_C8, d0.x), fmaf(Q.x, BPM_C8, d0.y));
+    d = make_float2(fmaf(Q.y, BPM_C8, d0.x), fmaf(-Q.x, BPM_C8, d0.y));
+  }
+}
+
 // 16-point DFT of v[0..15] as 4 x 4: k = 4 k1 + k2, m = m1 + 4 m2.
 // Forward: DFT4 over k1 (fixed k2), twiddle W16^(k2 m1), DFT4 over k2 (fixed m1);
-// the result y[m] is left in v[m] (natural order).
+// the result y[m] is left in v[m] (natural order).  FUSE: the W16^2 / W16^6
+// twiddles inside the second butterflies (fewer instructions; the march
+// kernels); otherwise each twiddle is rounded on its own (the 3D passes, where
+// the fused form cost registers and measured slower).
+template <bool FUSE = true>
 BPM_DEV void dft16_fwd(float2 (&v)[16]) {
 #pragma unroll
   for (int k2 = 0; k2 < 4; ++k2) dft4<false>(v[k2], v[k2 + 4], v[k2 + 8], v[k2 + 12]);
   v[5] = w16<1, false>(v[5]);
-  v[6] = w16<2, false>(v[6]);
   v[7] = w16<3, false>(v[7]);
-  v[9] = w16<2, false>(v[9]);
   v[10] = w16<4, false>(v[10]);
-  v[11] = w16<6, false>(v[11]);
   v[13] = w16<3, false>(v[13]);
-  v[14] = w16<6, false>(v[14]);
   v[15] = w16<9, false>(v[15]);
   // register 4 m1 + k2 holds u[k2][m1]
+  if constexpr (FUSE) {
+    // the twiddles of v6, v9 (W16^2) and v11, v14 (W16^6) inside the butterflies
+    dft4<false>(v[0], v[1], v[2], v[3]);
+    dft4_c<2, false>(v[4], v[5], v[6], v[7]);
+    dft4_bd<false>(v[8], v[9], v[10], v[11]);
+    dft4_c<6, false>(v[12], v[13], v[14], v[15]);
+  } else {
+    v[6] = w16<2, false>(v[6]);
+    v[9] = w16<2, false>(v[9]);
+    v[11] = w16<6, false>(v[11]);
+    v[14] = w16<6, false>(v[14]);
 #pragma unroll
-  for (int m1 = 0; m1 < 4; ++m1) dft4<false>(v[4 * m1], v[4 * m1 + 1], v[4 * m1 + 2], v[4 * m1 + 3]);
+    for (int m1 = 0; m1 < 4; ++m1)
+      dft4<false>(v[4 * m1], v[4 * m1 + 1], v[4 * m1 + 2], v[4 * m1 + 3]);
+  }
   // register 4 m1 + m2 holds y[m1 + 4 m2]: transpose (register renaming only)
   float2 o[16];
 #pragma unroll
@@ -172,6 +242,7 @@ BPM_DEV void dft16_fwd(float2 (&v)[16]) {
 }
 
 // Exact adjoint of dft16_fwd (unnormalised inverse DFT): y[m] in v[m] -> x[k] in v[k].
+template <bool FUSE = true>
 BPM_DEV void dft16_inv(float2 (&v)[16]) {
   float2 o[16];
 #pragma unroll
@@ -181,16 +252,24 @@ BPM_DEV void dft16_inv(float2 (&v)[16]) {
 #pragma unroll
   for (int m1 = 0; m1 < 4; ++m1) dft4<true>(o[4 * m1], o[4 * m1 + 1], o[4 * m1 + 2], o[4 * m1 + 3]);
   o[5] = w16<1, true>(o[5]);
-  o[6] = w16<2, true>(o[6]);
   o[7] = w16<3, true>(o[7]);
-  o[9] = w16<2, true>(o[9]);
   o[10] = w16<4, true>(o[10]);
-  o[11] = w16<6, true>(o[11]);
   o[13] = w16<3, true>(o[13]);
-  o[14] = w16<6, true>(o[14]);
   o[15] = w16<9, true>(o[15]);
+  if constexpr (FUSE) {
+    // o6, o9 (conj W16^2) and o11, o14 (conj W16^6) rotate inside the butterflies
+    dft4<true>(o[0], o[4], o[8], o[12]);
+    dft4_c<2, true>(o[1], o[5], o[9], o[13]);
+    dft4_bd<true>(o[2], o[6], o[10], o[14]);
+    dft4_c<6, true>(o[3], o[7], o[11], o[15]);
+  } else {
+    o[6] = w16<2, true>(o[6]);
+    o[9] = w16<2, true>(o[9]);
+    o[11] = w16<6, true>(o[11]);
+    o[14] = w16<6, true>(o[14]);
 #pragma unroll
-  for (int k2 = 0; k2 < 4; ++k2) dft4<true>(o[k2], o[k2 + 4], o[k2 + 8], o[k2 + 12]);
+    for (int k2 = 0; k2 < 4; ++k2) dft4<true>(o[k2], o[k2 + 4], o[k2 + 8], o[k2 + 12]);
+  }
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = o[i];
 }
@@ -236,10 +315,10 @@ BPM_DEV void dft8_inv(float2 (&v)[16]) {
 }
 
 // Last-stage butterflies: 16/R independent R-point DFTs on consecutive registers.
-template <int R, bool INV>
+template <int R, bool INV, bool FUSE = true>
 BPM_DEV void last_stage(float2 (&v)[16]) {
   if constexpr (R == 16) {
-    if (INV) dft16_inv(v); else dft16_fwd(v);
+    if (INV) dft16_inv<FUSE>(v); else dft16_fwd<FUSE>(v);
   } else if constexpr (R == 8) {
     if (INV) { dft8_inv<0>(v); dft8_inv<8>(v); } else { dft8_fwd<0>(v); dft8_fwd<8>(v); }
   } else if constexpr (R == 4) {

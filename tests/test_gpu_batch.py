@@ -241,3 +241,35 @@ def test_block_cap_and_rounds_in_flight(stream):
         assert_same(fetch(p), r)
         p.close()
     b.close()
+
+
+def test_full_uneven_batch_sampled_against_oracle(stream):
+    """The uneven batch at its full size (64 instances, seed 3, Nx 1024..8192,
+    Nz 500..4000, 128..1024 channels: the workload the batched bench times, in
+    one graph-captured pass): sampled channels of the largest transform and of
+    the longest march, plus a mid-size instance, against the oracle."""
+    import torch
+    ws = workloads.batch(n_inst=64, seed=3)
+    us = [None if w.u is None else torch.from_numpy(np.ascontiguousarray(w.u)).cuda()
+          for w in ws]
+    b = bpm.Batch(stream=stream)
+    plans = [bpm.plan_from_workload(w, stream=stream, u=u) for w, u in zip(ws, us)]
+    for p in plans:
+        b.submit(p)
+    b.run_graph()
+    b.sync()
+    big = max(range(len(ws)), key=lambda i: (ws[i].nx, ws[i].nz))
+    longest = max(range(len(ws)), key=lambda i: ws[i].nz * ws[i].nx)
+    mid = next(i for i, w in enumerate(ws) if w.nx == 2048)
+    for i in sorted({big, longest, mid}):
+        w = ws[i]
+        pick = [w.n_ch // 2, w.n_ch - 1]
+        o0, oh, init = orc.run(w.subset(pick))
+        g0, gh = plans[i].e0()[pick], plans[i].eh()[pick]
+        inc = np.linalg.norm(init, axis=1)
+        err = max(np.max(np.linalg.norm(g0 - o0, axis=1) / inc),
+                  np.max(np.linalg.norm(gh - oh, axis=1) / inc))
+        assert err < TOL_FIELD, (i, w.nx, w.nz, err)
+    for p in plans:
+        p.close()
+    b.close()

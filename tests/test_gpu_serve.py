@@ -68,3 +68,27 @@ def test_plain_server_matches_too():
     for r in reqs:
         R, eh = alone(r)
         assert np.array_equal(r.R, R) and np.array_equal(r.eh, eh)
+
+
+def test_served_results_match_oracle():
+    """The served form against the FP64 oracle: every instance (sampled
+    channels) and a spread of rocking-curve probes, Eh per channel within 1e-4
+    of the incident norm and R_i within 1e-5."""
+    import torch
+    import oracle.oracle as orc
+    torch.cuda.set_device(0)
+    reqs = requests(n_probe=30, seed=9)
+    srv = serve.Server(hbm_budget_bytes=int(64 * 2 ** 30), chunk=64, short_sms=4, short_cells=5e5)
+    srv.serve(reqs)
+    srv.close()
+    probes = [r for r in reqs if r.work.n_ch == 1]
+    checked = [r for r in reqs if r.work.n_ch > 1] + probes[::6]
+    for r in checked:
+        w = r.work
+        pick = sorted({0, w.n_ch - 1})
+        o0, oh, init = orc.run(w.subset(pick))
+        oR, _ = orc.reflectivity(init, o0, oh)
+        inc = np.linalg.norm(init, axis=1)
+        err = np.max(np.linalg.norm(r.eh[pick] - oh, axis=1) / inc)
+        assert err < 1e-4, (w.name, err)
+        assert np.max(np.abs(r.R[pick] - oR)) < 1e-5, w.name

@@ -3,15 +3,14 @@
 //
 // One channel per block of T = N/16 threads (16 positions each).  At Nx = 8192
 // both envelopes in registers need more than the 128 registers a 512-thread
-// block allows, and the spills went to DRAM.  At Nx <= 4096, with tables and
-// twiddles read from L2, the parked form needs at most 128 registers and
-// N (1 + 1/16 + 2) complex64 of shared memory (98 KB at 4096), so that two or
-// more channel blocks share an SM and run their exchanges and butterflies at
-// independent phases.  Here only one
+// block allows, and the spills went to DRAM.  At Nx <= 4096 the parked form
+// needs at most 128 registers and 3 (N + N/16) complex64 of shared memory
+// (102.5 KB at 4096), so that two or more channel blocks share an SM and run
+// their exchanges and butterflies at independent phases.  Here only one
 // envelope lives in registers at a time: the other is parked in shared memory
 // at the thread's own x positions (thread-private, so parking needs no
 // barrier), and the two envelopes run the same single-envelope transform one
-// after the other through a 64 KB exchange buffer.  The arithmetic of every
+// after the other.  The arithmetic of every
 // element is that of bpm_resident.cuh (same butterflies, twiddles, tables and
 // coupling, in the same order), so the fields are bitwise the same.
 //

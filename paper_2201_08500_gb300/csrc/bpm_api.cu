@@ -1278,7 +1278,7 @@ bpm_status enqueue_round(bpm_batch b, RoundSlot& r, int chunk) {
                 "batch kernel");
     off += cnt[q];
   }
-  const int n_big = cnt[kQueueTm8192] + cnt[kQueueBig2];
+  const int n_big = cnt[kQueueTm8192] + cnt[kQueueTm8192s2] + cnt[kQueueBig4];
   const int n_small = int(tmp.size()) - n_big;
   BPM_BCUDA(b, cudaEventRecord(r.free_ev, b->stream), "round event");
   r.used = true;

@@ -83,15 +83,22 @@ __global__ void __launch_bounds__(512, 1)
   }
 }
 
-// First-order items at Nx = 2048, 4096, 8192 in the parked form with the
-// tables in tensor memory (Parked<N, 1, true>, the fastest single-plan form
-// there): one channel per item, N/16 threads per block, 512/(N/16) blocks per
-// SM; every block allocates its TMEM columns once and frees them on exit.
-template <int N>
+// Body of the TMEM queues: first order in the narrow layout (fewer spills in
+// the work-queue kernel, measured faster), Strang in the layout of its
+// single-plan kernel (wide at N <= 4096).
+template <int N, int SPLIT>
+using TmBody = Parked<N, SPLIT, true, SPLIT == 2 && N <= 4096>;
+
+// First-order and Strang items at Nx = 2048, 4096, 8192 in the parked form
+// with the tables in tensor memory (Parked<N, SPLIT, true>, the fastest
+// single-plan form there): one channel per item, N/16 threads per block,
+// 512/(N/16) blocks per SM; every block allocates its TMEM columns once and
+// frees them on exit.
+template <int N, int SPLIT>
 __global__ void __launch_bounds__(N / 16, 512 / (N / 16))
     batch_kernel_tm(const MarchArgs* __restrict__ plans, const BatchItem* __restrict__ items,
                     int n_items, int* counter) {
-  using P = Parked<N, 1, true, false>;
+  using P = TmBody<N, SPLIT>;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
   __shared__ uint32_t s_tbase;
@@ -112,12 +119,34 @@ __global__ void __launch_bounds__(N / 16, 512 / (N / 16))
   if (threadIdx.x / 32 == 0) tmem_dealloc<P::kCols>(s_tbase);
 }
 
+// Fourth-order items at Nx = 1024, 2048, 4096 in the parked form with both
+// table sets read from L2 (Parked<N, 4>, the fastest single-plan form there):
+// one channel per item, N/16 threads per block, 512/(N/16) blocks per SM.
+template <int N, int SPLIT>
+__global__ void __launch_bounds__(N / 16, 512 / (N / 16))
+    batch_kernel_pk(const MarchArgs* __restrict__ plans, const BatchItem* __restrict__ items,
+                    int n_items, int* counter) {
+  using P = Parked<N, SPLIT>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_item;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= n_items) break;
+    const BatchItem item = items[it];
+    P::run_item(plans[item.plan], item.ch0, smem);
+  }
+}
+
 }  // namespace
 
 int batch_group(int n) { return n == 8192 ? 1 : kSmallThreads / (n / 16); }
 
 int batch_item_channels(int n, int split_order) {
-  return (split_order == 1 && n >= 2048) ? 1 : batch_group(n);
+  const bool parked = (split_order <= 2 && n >= 2048) || (split_order == 4 && n >= 1024 && n <= 4096);
+  return parked ? 1 : batch_group(n);
 }
 
 int batch_queue(int n, int split_order) {
@@ -127,49 +156,87 @@ int batch_queue(int n, int split_order) {
     if (n == 2048) return kQueueTm2048;
     return kQueueSmall;
   }
-  if (split_order == 4) return n == 8192 ? kQueueBig4 : kQueueSmall4;
-  return n == 8192 ? kQueueBig2 : kQueueSmall2;
+  if (split_order == 4) {
+    if (n == 8192) return kQueueBig4;
+    if (n == 4096) return kQueuePk4096s4;
+    if (n == 2048) return kQueuePk2048s4;
+    if (n == 1024) return kQueuePk1024s4;
+    return kQueueSmall4;
+  }
+  if (n == 8192) return kQueueTm8192s2;
+  if (n == 4096) return kQueueTm4096s2;
+  if (n == 2048) return kQueueTm2048s2;
+  return kQueueSmall2;
 }
 
 int batch_blocks_per_sm(int queue) {
   switch (queue) {
-    case kQueueTm4096: return 2;
-    case kQueueTm2048: return 4;
+    case kQueueTm4096:
+    case kQueueTm4096s2:
+    case kQueuePk4096s4: return 2;
+    case kQueueTm2048:
+    case kQueueTm2048s2:
+    case kQueuePk2048s4: return 4;
+    case kQueuePk1024s4: return 8;
     default: return 1;
   }
 }
 
+namespace {
+
+template <int N, int SPLIT>
+void tm_launch(const MarchArgs* plans, const BatchItem* items, int n_items, int* counter,
+               int blocks, cudaStream_t s) {
+  batch_kernel_tm<N, SPLIT><<<blocks, N / 16, TmBody<N, SPLIT>::smem_bytes(), s>>>(
+      plans, items, n_items, counter);
+}
+
+template <int N, int SPLIT>
+void pk_launch(const MarchArgs* plans, const BatchItem* items, int n_items, int* counter,
+               int blocks, cudaStream_t s) {
+  batch_kernel_pk<N, SPLIT><<<blocks, N / 16, Parked<N, SPLIT>::smem_bytes(), s>>>(
+      plans, items, n_items, counter);
+}
+
+template <int N, int SPLIT>
+cudaError_t tm_attr() {
+  return cudaFuncSetAttribute(batch_kernel_tm<N, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(TmBody<N, SPLIT>::smem_bytes()));
+}
+
+template <int N, int SPLIT>
+cudaError_t pk_attr() {
+  return cudaFuncSetAttribute(batch_kernel_pk<N, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(Parked<N, SPLIT>::smem_bytes()));
+}
+
+}  // namespace
+
 cudaError_t launch_batch(const MarchArgs* plans, const BatchItem* items, int n_items, int* counter,
                          int queue, int blocks, cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
-  const size_t big_smem = Parked<8192, 1>::smem_bytes();
+  const size_t big_smem = Parked<8192, 4>::smem_bytes();
   switch (queue) {
-    case kQueueTm8192:
-      batch_kernel_tm<8192><<<blocks, 512, Parked<8192, 1, true, false>::smem_bytes(), s>>>(
-          plans, items, n_items, counter);
-      break;
-    case kQueueTm4096:
-      batch_kernel_tm<4096><<<blocks, 256, Parked<4096, 1, true, false>::smem_bytes(), s>>>(
-          plans, items, n_items, counter);
-      break;
-    case kQueueTm2048:
-      batch_kernel_tm<2048><<<blocks, 128, Parked<2048, 1, true, false>::smem_bytes(), s>>>(
-          plans, items, n_items, counter);
-      break;
+    case kQueueTm8192: tm_launch<8192, 1>(plans, items, n_items, counter, blocks, s); break;
+    case kQueueTm4096: tm_launch<4096, 1>(plans, items, n_items, counter, blocks, s); break;
+    case kQueueTm2048: tm_launch<2048, 1>(plans, items, n_items, counter, blocks, s); break;
+    case kQueueTm8192s2: tm_launch<8192, 2>(plans, items, n_items, counter, blocks, s); break;
+    case kQueueTm4096s2: tm_launch<4096, 2>(plans, items, n_items, counter, blocks, s); break;
+    case kQueueTm2048s2: tm_launch<2048, 2>(plans, items, n_items, counter, blocks, s); break;
+    case kQueuePk4096s4: pk_launch<4096, 4>(plans, items, n_items, counter, blocks, s); break;
+    case kQueuePk2048s4: pk_launch<2048, 4>(plans, items, n_items, counter, blocks, s); break;
+    case kQueuePk1024s4: pk_launch<1024, 4>(plans, items, n_items, counter, blocks, s); break;
     case kQueueSmall:
       batch_kernel<1><<<blocks, kSmallThreads, kSmallSmem, s>>>(plans, items, n_items, counter);
-      break;
-    case kQueueBig2:
-      batch_kernel_8192<2><<<blocks, 512, big_smem, s>>>(plans, items, n_items, counter);
       break;
     case kQueueSmall2:
       batch_kernel<2><<<blocks, kSmallThreads, kSmallSmem, s>>>(plans, items, n_items, counter);
       break;
-    case kQueueBig4:
-      batch_kernel_8192<4><<<blocks, 512, big_smem, s>>>(plans, items, n_items, counter);
-      break;
     case kQueueSmall4:
       batch_kernel<4><<<blocks, kSmallThreads, kSmallSmem, s>>>(plans, items, n_items, counter);
+      break;
+    case kQueueBig4:
+      batch_kernel_8192<4><<<blocks, 512, big_smem, s>>>(plans, items, n_items, counter);
       break;
     default:
       return cudaErrorInvalidValue;
@@ -178,17 +245,15 @@ cudaError_t launch_batch(const MarchArgs* plans, const BatchItem* items, int n_i
 }
 
 cudaError_t batch_set_attributes() {
-  const int small = int(kSmallSmem), big = int(Parked<8192, 1>::smem_bytes());
+  const int small = int(kSmallSmem), big = int(Parked<8192, 4>::smem_bytes());
   const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t r[] = {
-      cudaFuncSetAttribute(batch_kernel<1>, attr, small),
-      cudaFuncSetAttribute(batch_kernel<2>, attr, small),
-      cudaFuncSetAttribute(batch_kernel<4>, attr, small),
-      cudaFuncSetAttribute(batch_kernel_8192<2>, attr, big),
-      cudaFuncSetAttribute(batch_kernel_8192<4>, attr, big),
-      cudaFuncSetAttribute(batch_kernel_tm<8192>, attr, int(Parked<8192, 1, true, false>::smem_bytes())),
-      cudaFuncSetAttribute(batch_kernel_tm<4096>, attr, int(Parked<4096, 1, true, false>::smem_bytes())),
-      cudaFuncSetAttribute(batch_kernel_tm<2048>, attr, int(Parked<2048, 1, true, false>::smem_bytes()))};
+  cudaError_t r[] = {cudaFuncSetAttribute(batch_kernel<1>, attr, small),
+                     cudaFuncSetAttribute(batch_kernel<2>, attr, small),
+                     cudaFuncSetAttribute(batch_kernel<4>, attr, small),
+                     cudaFuncSetAttribute(batch_kernel_8192<4>, attr, big),
+                     tm_attr<8192, 1>(), tm_attr<4096, 1>(), tm_attr<2048, 1>(),
+                     tm_attr<8192, 2>(), tm_attr<4096, 2>(), tm_attr<2048, 2>(),
+                     pk_attr<4096, 4>(), pk_attr<2048, 4>(), pk_attr<1024, 4>()};
   for (cudaError_t e : r)
     if (e != cudaSuccess) return e;
   return cudaSuccess;

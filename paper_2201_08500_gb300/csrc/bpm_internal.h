@@ -82,13 +82,18 @@ struct BatchItem {
 // launched back to back in this order (longest items first within each):
 enum BatchQueue {
   kQueueTm8192 = 0,  // first order, Nx = 8192: parked form, TMEM tables
-  kQueueBig2,        // Strang, Nx = 8192: parked form, L2 tables
   kQueueTm4096,      // first order, Nx = 4096: parked form, TMEM tables, 2 blocks / SM
   kQueueTm2048,      // first order, Nx = 2048: parked form, TMEM tables, 4 blocks / SM
   kQueueSmall,       // first order, Nx <= 1024: resident form, G channels per block
-  kQueueSmall2,      // Strang, Nx <= 4096: resident form
+  kQueueSmall2,      // Strang, Nx <= 1024: resident form
   kQueueBig4,        // fourth order, Nx = 8192: parked form, L2 tables (two sets)
-  kQueueSmall4,      // fourth order, Nx <= 4096: resident form, L2 tables (two sets)
+  kQueueSmall4,      // fourth order, Nx <= 512: resident form, L2 tables (two sets)
+  kQueueTm8192s2,    // Strang, Nx = 8192: parked form, TMEM tables
+  kQueueTm4096s2,    // Strang, Nx = 4096: parked form, TMEM tables, 2 blocks / SM
+  kQueueTm2048s2,    // Strang, Nx = 2048: parked form, TMEM tables, 4 blocks / SM
+  kQueuePk4096s4,    // fourth order, Nx = 4096: parked form, L2 tables, 2 blocks / SM
+  kQueuePk2048s4,    // fourth order, Nx = 2048: parked form, L2 tables, 4 blocks / SM
+  kQueuePk1024s4,    // fourth order, Nx = 1024: parked form, L2 tables, 8 blocks / SM
   kQueueCount
 };
 int batch_group(int n);                               // channels per block of the resident kernels

@@ -220,6 +220,26 @@ def test_fourth_order_plans_in_a_mixed_batch(stream):
         assert err < TOL_FIELD, (w.name, err)
 
 
+def test_strang_and_fourth_order_parked_queues(stream):
+    """The parked queues of the higher orders: Strang at Nx = 2048, 4096, 8192
+    (tables in TMEM) and fourth order at Nx = 1024, 2048, 4096 (tables from
+    L2), in one batch; each plan equals its single-plan march bitwise."""
+    ws = mix(seed=31)[:4] + mix(seed=37)[:3]   # Nx 1024, 2048, 4096, 8192, 1024, 2048, 4096
+    for w, order in zip(ws, (4, 2, 2, 2, 4, 4, 4)):
+        w.split_order = order
+    ref = [single(w, stream) for w in ws]
+    b = bpm.Batch(stream=stream)
+    plans = [bpm.plan_from_workload(w, stream=stream) for w in ws]
+    for p in plans:
+        b.submit(p)
+    b.run()
+    b.sync()
+    for p, r in zip(plans, ref):
+        assert_same(fetch(p), r)
+        p.close()
+    b.close()
+
+
 def test_block_cap_and_rounds_in_flight(stream):
     """A batch capped at 3 blocks gives the same fields; pending() counts rounds
     whose kernels have not finished and is 0 after a sync."""

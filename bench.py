@@ -10,16 +10,27 @@ cell-updates per second (channel x transverse cell x z step).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-N > 1 runs under torchrun: every rank marches an independent instance of the
-same size (weak scaling); there is no data-path collective.  With
---shard-channels the ranks instead split one instance's channels into
-contiguous blocks and sum-reduce its time response, the one exchange of a
-sharded pulse (strong scaling).  --impl reference times the FP64 CPU oracle on
-the host cores on a bounded channel sample.
+At N = 1 the one JSON line also carries, as nested objects, the other
+workloads of the method: `batched` (64 uneven instances in one CUDA graph of
+persistent work-queue launches against one launch per instance), `served` (a
+Poisson stream of 10,000 requests served with continuous batching against
+plain per-request launches, p50/p99 latency) and `3d` (512 x 512 transverse,
+1000 steps, 128 channels, HBM-streamed, against the HBM roofline).  Each has
+its own clock record and a parity sample against the FP64 oracle; the oracle
+samples run on the host in a background thread while the GPU goes on.
+--no-extras skips them.  `peaks` holds the measured FP32 and FP64 CUDA-core
+rates (FMA chains on every SM) that the ALU rooflines divide by.
+
+N > 1 runs under torchrun: the ranks split ONE instance's channels into
+contiguous blocks (strong scaling) and reduce-scatter its time response over
+t, the one exchange of a sharded pulse.  --independent instead marches one
+instance per rank (weak scaling, no data-path collective).  --impl reference
+times the FP64 CPU oracle on the host cores on a bounded channel sample.
 """
 from __future__ import annotations
 
 import argparse
+import concurrent.futures as cf
 import json
 import math
 import os
@@ -37,24 +48,34 @@ sys.path.insert(0, ROOT)
 from paper_2201_08500_gb300 import workloads  # noqa: E402
 
 METRIC = "BPM cell-updates/s (omega*x*z)"
+UNIT = "cell-updates/s"
+FP32_LANES_PER_SM = 128
+TOL_FIELD = 1e-4
+TOL_R = 1e-5
+
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
 # default march, from one ncu capture of that launch per launch form: form 0
 # 597.55 MB read + 62.88 MB written, form 3 535.22 + 54.93 MB.  The deformation
 # rows are re-read by each wave of channels, which at ~9 GB/s is immaterial to
 # this ALU-bound kernel.  Keyed by kernel, form and workload; any other
 # configuration reports null.
+MEASURED_TRAFFIC = {
+    ("march_kernel<4096,1> form 0", "deformed-2d-nx4096-nz2000-ch1024", 1): 660.43e6,
+    ("march_kernel<4096,1> form 3", "deformed-2d-nx4096-nz2000-ch1024", 1): 590.15e6,
+}
+# Executed FP32 flop per cell-update (FADD + FMUL + 2 FFMA thread instructions,
+# ncu, per kernel and form): the work the kernel really issues, against the
+# nominal count of flops_per_cell.
+EXECUTED_FLOPS = {
+    "march_kernel<4096,1> form 3": 210.0,
+    "march_kernel<8192,1> form 3": 240.0,
+}
 # DRAM bytes of one z step of the 3D workload (one column pass + one MODE-1 row
 # pass, 256-thread row tile), from the live launch list of those launches with
 # --cache-control none: 1239 + 1085 MB.  Algorithmic: 64 B per cell-update =
 # 2147 MB; the excess is the row pass's output draining from L2 during the
 # column pass.
 MEASURED_TRAFFIC_3D = {("large-3d-512x512-nz1000-ch128", 0, 256): 2323.87e6}
-MEASURED_TRAFFIC = {
-    ("march_kernel<4096,1> form 0", "deformed-2d-nx4096-nz2000-ch1024", 1): 660.43e6,
-    ("march_kernel<4096,1> form 3", "deformed-2d-nx4096-nz2000-ch1024", 1): 590.15e6,
-}
-UNIT = "cell-updates/s"
-FP32_LANES_PER_SM = 128
 
 
 def flops_per_cell(n: int, split_order: int = 1) -> float:
@@ -95,6 +116,7 @@ class ClockSampler:
             self.thread.start()
         except Exception:
             self.proc = None
+        return self
 
     def _read(self):
         for line in self.proc.stdout:
@@ -108,7 +130,7 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
+        sm, smax, power, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
@@ -117,6 +139,7 @@ class ClockSampler:
             try:
                 sm.append(float(parts[1]))
                 smax.append(float(parts[2]))
+                power.append(float(parts[3]))
             except ValueError:
                 continue
             for nm, val in zip(names, parts[5:9]):
@@ -124,7 +147,7 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
 def dist_env():
@@ -132,12 +155,6 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
-
-
-def rank_workload(n_ch: int, nx: int, nz: int, rank: int):
-    """Each rank marches its own instance of the same size (seed 2 + rank):
-    channels and instances are independent, so ranks exchange no data."""
-    return workloads.deformed(n_ch=n_ch, nx=nx, nz=nz, seed=2 + rank)
 
 
 def max_over_ranks(value: float, dist=None, device="cpu") -> float:
@@ -155,6 +172,26 @@ def whole_job_value(world: int, cells_per_rank: int, ms: float) -> float:
     return world * cells_per_rank / (ms * 1e-3)
 
 
+def rank_workload(n_ch: int, nx: int, nz: int, rank: int):
+    """--independent: each rank marches its own instance of the same size
+    (seed 2 + rank); channels and instances are independent, so ranks exchange
+    no data."""
+    return workloads.deformed(n_ch=n_ch, nx=nx, nz=nz, seed=2 + rank)
+
+
+def rank_share(n_ch: int, nx: int, nz: int, world: int, rank: int):
+    """Default at N > 1: the ranks split ONE instance (seed 2) into contiguous
+    channel blocks.  Returns (this rank's workload, the whole instance, its
+    first channel); the job's work is the whole instance's cell-updates."""
+    from paper_2201_08500_gb300 import shard
+    w_all = workloads.deformed(n_ch=n_ch, nx=nx, nz=nz, seed=2)
+    first, cnt = shard.channel_blocks(w_all.n_ch, world)[rank]
+    if cnt == 0:
+        raise SystemExit("a sharded pulse needs at least one channel per rank")
+    return w_all.subset(list(range(first, first + cnt))), w_all, first
+
+
+# --------------------------------------------------------------------------- oracle legs
 def oracle_sample(w, n_channels: int, n_threads: int, keep: bool = False):
     """Time the FP64 oracle (as it stands) on n_channels channels of workload w
     spread over the band; keep=True also returns (channel indices, e0, eh, init)."""
@@ -170,41 +207,113 @@ def oracle_sample(w, n_channels: int, n_threads: int, keep: bool = False):
     return cells / dt, dt, cells
 
 
+def field_errors(w, channels, g0, gh, n_threads):
+    """GPU fields g0, gh ([len(channels), plane], the final z) of channels of
+    workload w against the oracle: per-channel error relative to the incident
+    field's norm, rel-L2 of each field, and R_i."""
+    import oracle.oracle as orc
+    o0, oh, init = orc.run(w, channels=channels, n_threads=n_threads)
+    g0 = np.asarray(g0).reshape(len(channels), -1)
+    gh = np.asarray(gh).reshape(len(channels), -1)
+    inc = np.linalg.norm(init, axis=1)
+    err = np.maximum(np.linalg.norm(g0 - o0, axis=1), np.linalg.norm(gh - oh, axis=1)) / inc
+    oR, _ = orc.reflectivity(init, o0, oh)
+    return dict(max_err_per_channel=float(err.max()), median_err_per_channel=float(np.median(err)),
+                rel_l2_e0=float(np.linalg.norm(g0 - o0) / np.linalg.norm(o0)),
+                rel_l2_eh=float(np.linalg.norm(gh - oh) / np.linalg.norm(oh))), oR
+
+
+class OracleJobs:
+    """Parity samples against the FP64 oracle, run one after another in a
+    background thread (the oracle's C march releases the GIL) while the GPU
+    sections go on; `threads` host threads each."""
+
+    def __init__(self, threads: int):
+        self.threads = max(1, threads)
+        self.pool = cf.ThreadPoolExecutor(max_workers=1)
+        self.jobs = {}
+
+    def submit(self, name, fn, *args):
+        self.jobs[name] = (time.perf_counter(), self.pool.submit(fn, *args))
+
+    def result(self, name):
+        t0, fut = self.jobs[name]
+        try:
+            out = fut.result()
+        except Exception as e:  # reported in the line, never silently dropped
+            out = {"error": repr(e)[:300]}
+        return out
+
+    def close(self):
+        self.pool.shutdown(wait=True)
+
+
 def run_reference(args, world, rank):
+    """The FP64 oracle as it stands, on the host cores: each step is one bounded
+    sample of the workload (2 channels per core, spread over the band, full
+    march).  ms_per_step is the sample's own time; value is the sample's
+    cell-updates per second."""
     if rank != 0:
         return 0
     w = workloads.deformed(n_ch=args.channels, nx=args.nx, nz=args.nz)
     cores = os.cpu_count() or 1
-    n = max(1, min(w.n_ch, 2 * cores))  # 2 channels per core, full march, per step
+    n = max(1, min(w.n_ch, 2 * cores))
     for _ in range(args.warmup):
         oracle_sample(w.subset(range(0, w.n_ch, max(1, w.n_ch // n))), 1, 1)
-    vals = []
-    t_all = 0.0
+    vals, dts = [], []
     for _ in range(args.steps):
         v, dt, cells = oracle_sample(w, n, cores)
         vals.append(v)
-        t_all += dt
+        dts.append(dt)
     value = statistics.median(vals)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * w.cell_updates / value, "higher_is_better": True,
+        "ms_per_step": 1e3 * statistics.median(dts), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "nx": w.nx, "nz": w.nz, "channels": w.n_ch,
-                   "l2": "n/a (CPU)"},
+                   "l2": "n/a (CPU)",
+                   "step": f"one sample of {n} of the {w.n_ch} channels (full {w.nz}-step "
+                           f"march each); ms_per_step is the sample's time"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{n} of {w.n_ch} channels, full {w.nz}-step march, "
-                                   f"per step; throughput scaled per cell-update"},
+                                   f"per step; throughput per cell-update of the sample"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_batched(args, world, rank, local):
+# --------------------------------------------------------------------------- measured peaks
+def measure_cuda_core_peaks(local: int) -> dict:
+    """FP32 (FFMA) and FP64 (DFMA) chains on every SM (bpm_measure_peak): each
+    launch sized to ~150 ms, median of 5, SM clock sampled during them."""
+    import torch
+    from paper_2201_08500_gb300 import bpm
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    out = {}
+    for kind, name, iters in ((bpm.BPM_PEAK_FP32, "fp32", 1 << 18),
+                              (bpm.BPM_PEAK_FP64, "fp64", 1 << 12)):
+        bpm.measure_peak(kind, max(1, iters // 16))
+        _, ms = bpm.measure_peak(kind, iters)
+        iters = max(1, int(iters * 150.0 / max(ms, 1e-3)))
+        sampler = ClockSampler(local).start()
+        runs = [bpm.measure_peak(kind, iters) for _ in range(5)]
+        clocks = sampler.stop()
+        rate = statistics.median(r for r, _ in runs)
+        mhz = clocks.get("sm_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
+        out[name] = {"tflops": rate / 1e12, "launch_ms": statistics.median(m for _, m in runs),
+                     "flop_per_clock_per_sm": rate / (sms * mhz * 1e6), "clocks": clocks,
+                     "how": "independent FMA chains, 1024 threads per SM (bpm_measure_peak)"}
+    return out
+
+
+# --------------------------------------------------------------------------- config 3
+def run_batched(args, world, rank, local, jobs=None):
     """Uneven batch: every instance's full hot path (setup, march, time response),
-    once as one CUDA graph around the work-queue launch, once as one march launch
-    per instance (the plain form), on the same plans."""
+    once as one CUDA graph around the work-queue launches, once as one march
+    launch per instance (the plain form), on the same plans.  Returns the
+    `batched` object; with jobs, sampled channels go to the oracle."""
     import torch
     from paper_2201_08500_gb300 import bpm
 
@@ -213,7 +322,7 @@ def run_batched(args, world, rank, local):
     stream = torch.cuda.current_stream()
     us = [None if w.u is None else torch.from_numpy(np.ascontiguousarray(w.u)).cuda() for w in ws]
     # the plain form runs each instance in the launch form the autotuner picks
-    # for its shape (untimed setup); the work-queue kernels use the shared-memory form
+    # for its shape (untimed setup)
     tuned = {}
     for w in ws:
         key = (w.nx, w.n_ch)
@@ -248,40 +357,65 @@ def run_batched(args, world, rank, local):
             out.append(e0.elapsed_time(e1))
         return statistics.median(out)
 
-    sampler = ClockSampler(local)
-    sampler.start()
-    ms_batched = timed(b.run_graph, args.steps, max(3, args.warmup))
+    steps_b = max(3, min(args.steps, args.extra_steps))
+    sampler = ClockSampler(local).start()
+    ms_batched = timed(b.run_graph, steps_b, 3)
     clocks = sampler.stop()
-    ms_plain = timed(plain_step, max(2, args.steps // 2), 1)
+    # parity sample: per transform size the instance with the most z steps,
+    # its first, middle and last channel (fields of the last graph pass)
+    picks = []
+    for nx in sorted({w.nx for w in ws}):
+        i = max((k for k, w in enumerate(ws) if w.nx == nx), key=lambda k: ws[k].nz)
+        chs = sorted({0, ws[i].n_ch // 2, ws[i].n_ch - 1})
+        picks.append((i, chs, plans[i].e0()[chs], plans[i].eh()[chs], plans[i].reflectivity()[0]))
+    steps_p = max(2, steps_b // 2)
+    ms_plain = timed(plain_step, steps_p, 1)
+    # the plain launches recompute the same fields: alone == in the work queue
+    same = all(np.array_equal(plans[i].eh()[chs], gh) and np.array_equal(plans[i].e0()[chs], g0)
+               for i, chs, g0, gh, _ in picks)
     info = b.info()
-    line = {
+    out = {
         "metric": METRIC + ", batched vs plain", "value": cells / (ms_batched * 1e-3), "unit": UNIT,
-        "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
-        "ms_per_step": ms_batched, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "c64 fields / f32 butterflies (f64 setup and time sum)",
-        "data": "synthetic",
-        "config": {"workload": f"uneven batch of {len(ws)} instances (seed {3 + rank})",
-                   "cell_updates": cells, "nx": sorted({w.nx for w in ws}),
-                   "l2": "flushed between timed steps (256 MB write)",
-                   "form": "one CUDA graph: setup of every instance, persistent work-queue "
-                           "march (Nx<=4096 kernel + Nx=8192 kernel), time responses"},
-        "plain": {"value": cells / (ms_plain * 1e-3), "ms_per_step": ms_plain,
-                  "form": "per instance: setup kernels, one march launch, time response"},
+        "steps": steps_b, "warmup": 3, "ms_per_step": ms_batched,
+        "workload": f"uneven batch of {len(ws)} instances (seed {3 + rank}): Nx in "
+                    f"{sorted({w.nx for w in ws})}, {min(w.nz for w in ws)}-"
+                    f"{max(w.nz for w in ws)} z steps, {min(w.n_ch for w in ws)}-"
+                    f"{max(w.n_ch for w in ws)} channels, perfect / bent / random strain",
+        "cell_updates": cells, "l2": "flushed between timed steps (256 MB write)",
+        "form": "one CUDA graph: setup of every instance, persistent work-queue launches "
+                "(13 queues by size and splitting order), time responses",
+        "plain": {"value": cells / (ms_plain * 1e-3), "ms_per_step": ms_plain, "steps": steps_p,
+                  "form": "per instance: setup kernels, one march launch in its tuned form, "
+                          "time response"},
         "speedup_vs_plain": ms_plain / ms_batched,
         "plain_launch_forms": sorted({(k[0], k[1], v["form"], v["channels_per_block"])
                                       for k, v in tuned.items()}),
         "items": info["last_items"], "clocks": clocks,
-        "gpu_launches": b.graph_kernels() * args.steps,
+        "gpu_launches": b.graph_kernels() * steps_b,
+        "results_equal_batched_vs_plain": bool(same),
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+
+    def parity():
+        worst, rows = {}, []
+        for i, chs, g0, gh, R in picks:
+            e, oR = field_errors(ws[i], chs, g0, gh, jobs.threads)
+            rows.append({"instance": ws[i].name, "channels": chs, **e,
+                         "max_abs_err_R": float(np.max(np.abs(R[chs] - oR)))})
+        for key in ("max_err_per_channel", "rel_l2_eh", "rel_l2_e0", "max_abs_err_R"):
+            worst[key] = max(r[key] for r in rows)
+        return {"vs": "FP64 oracle", "channels": sum(len(r["channels"]) for r in rows),
+                **worst, "tolerance": TOL_FIELD, "tolerance_R": TOL_R, "samples": rows}
+
+    if jobs is not None:
+        jobs.submit("batched", parity)
     for p in plans:
         p.close()
     b.close()
-    return 0
+    return out
 
 
-def run_3d(args, world, rank, local):
+# --------------------------------------------------------------------------- config 5
+def run_3d(args, world, rank, local, jobs=None):
     """3D (x, y, z) workload: 512 x 512 transverse, 1000 steps, 128 channels,
     HBM-streamed (two passes per step, 64 B of algorithmic traffic per
     cell-update); roofline against the measured HBM copy bandwidth."""
@@ -292,7 +426,8 @@ def run_3d(args, world, rank, local):
     nz = 1000 if args.nz == 2000 else args.nz
     n_ch = 128 if args.channels == 1024 else args.channels
     w = workloads.large_3d(n_ch=n_ch, nz=nz, seed=5 + rank)
-    u_dev = torch.from_numpy(np.ascontiguousarray(w.u)).cuda()
+    u_host = w.u
+    u_dev = torch.from_numpy(np.ascontiguousarray(u_host)).cuda()
     w.u = None
     stream = torch.cuda.current_stream()
     # launch form chosen by the autotuner (untimed setup): column-pass form and
@@ -311,13 +446,13 @@ def run_3d(args, world, rank, local):
         plan.set_pulse(w.omega, w.S, w.theta_i, w.x0, w.w0, w.zx, w.zR)
         plan.run()
 
-    for _ in range(max(3, args.warmup)):
+    for _ in range(3):
         step()
     torch.cuda.synchronize()
-    sampler = ClockSampler(local)
-    sampler.start()
+    steps = max(3, min(args.steps, args.extra_steps))
+    sampler = ClockSampler(local).start()
     times, march = [], []
-    for i in range(args.steps):
+    for i in range(steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         step()
@@ -333,32 +468,47 @@ def run_3d(args, world, rank, local):
     bytes_alg = 64.0 * cells
     achieved = bytes_alg / (march_ms * 1e-3) / 1e9
     peak = measured_peaks().get("hbm_gbs", 6800.0)
-    line = {
+    launch = plan.launch()
+    out = {
         "metric": METRIC + " (omega*x*y*z), 3D", "value": cells / (ms * 1e-3), "unit": UNIT,
-        "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "c64 fields / f32 butterflies (f64 setup and time sum)", "data": "synthetic",
-        "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "nz": w.nz, "channels": w.n_ch,
-                   "l2": "fields (512 MB) exceed L2 (129 MB)", "launch": plan.launch(),
-                   "tuned": tried},
+        "steps": steps, "warmup": 3, "ms_per_step": ms,
+        "workload": w.name, "nx": w.nx, "ny": w.ny, "nz": w.nz, "channels": w.n_ch,
+        "l2": "fields (512 MB) exceed L2 (129 MB)", "launch": launch, "tuned": tried,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
+                     "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                      "traffic": MEASURED_TRAFFIC_3D.get(
-                         (w.name, plan.launch()["form"], plan.launch()["row_threads"])),
+                         (w.name, launch["form"], launch["row_threads"])),
                      "traffic_unit": "one z step: column pass + row pass",
                      "algorithmic_bytes": 64 * w.n_ch * w.plane,
                      "kernel": "row_pass_kernel + col_pass_kernel (2 passes per z step)",
                      "bytes_per_cell_update": 64, "march_ms": march_ms,
                      "passes": st["march_launches"]},
-        "gpu_launches": st["launches"] + 4, "clocks": clocks,
+        "gpu_launches": (st["launches"] + 4) * steps, "clocks": clocks,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    if jobs is not None:
+        chs = [0, w.n_ch // 2]
+        g0 = torch.empty((w.n_ch, w.plane), dtype=torch.complex64, device="cuda")
+        gh = torch.empty_like(g0)
+        plan.fetch(bpm.BPM_FIELD_E0, out=g0)
+        plan.fetch(bpm.BPM_FIELD_EH, out=gh)
+        g0, gh = g0[chs].cpu().numpy(), gh[chs].cpu().numpy()
+        R = plan.reflectivity()[0]
+        w.u = u_host
+
+        def parity():
+            e, oR = field_errors(w, chs, g0, gh, min(jobs.threads, len(chs)))
+            return {"vs": "FP64 oracle", "channels": chs, **e,
+                    "max_abs_err_R": float(np.max(np.abs(R[chs] - oR))),
+                    "tolerance": TOL_FIELD, "tolerance_R": TOL_R}
+
+        jobs.submit("3d", parity)
     plan.close()
-    return 0
+    return out
 
 
-def run_served(args, world, rank, local):
+# --------------------------------------------------------------------------- config 4
+def run_served(args, world, rank, local, jobs=None):
     """Poisson stream of requests (80 % single-channel rocking-curve probes
     Nx = 512 / 300 steps, 20 % instances drawn from the uneven batch), offered at
     `load` x the measured capacity of the batched executor.  Three forms on the
@@ -416,14 +566,15 @@ def run_served(args, world, rank, local):
         return st
 
     served = make()
-    sampler = ClockSampler(local)  # clocks during the served (headline) run
-    sampler.start()
+    sampler = ClockSampler(local).start()  # clocks during the served (headline) run
     s_stats = served_form(served, 4)
     clocks = sampler.stop()
     one = make()
     o_stats = served_form(one, 0)
     plain = make()
+    p_sampler = ClockSampler(local).start()
     serve.serve_plain(plain, keep_fields=False)
+    p_clocks = p_sampler.stop()
     p_stats = serve.summarize(plain)
     same = all(np.array_equal(a.R, c.R) and np.array_equal(a.R, d.R)
                for a, c, d in zip(served, plain, one))
@@ -433,28 +584,58 @@ def run_served(args, world, rank, local):
     pb = make(n_burst, burst=True)
     serve.serve_plain(pb, keep_fields=False)
     pb_stats = serve.summarize(pb)
-    line = {
+    out = {
         "metric": METRIC + " served vs plain; p50/p99 latency", "value": s_stats["throughput"],
-        "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": 1,
-        "ms_per_step": s_stats["makespan_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "c64 fields / f32 butterflies", "data": "synthetic",
-        "config": {"workload": f"Poisson stream of {len(served)} requests (80 % probes Nx=512 "
-                               f"Nz=300 1 channel, 20 % uneven-batch instances), offered load "
-                               f"{args.load} x capacity {capacity:.3e} cell-updates/s; burst: "
-                               f"the first {n_burst} requests all at t = 0",
-                   "rate_per_s": rate, "chunk_steps": 256, "hbm_budget_gb": 96,
-                   "short_lane_sms": 4},
+        "unit": UNIT, "ms_per_step": s_stats["makespan_s"] * 1e3,
+        "workload": f"Poisson stream of {len(served)} requests (80 % probes Nx=512 Nz=300 "
+                    f"1 channel, 20 % uneven-batch instances), offered load {args.load} x "
+                    f"capacity {capacity:.3e} cell-updates/s; burst: the first {n_burst} "
+                    f"requests all at t = 0",
+        "rate_per_s": rate, "chunk_steps": 256, "hbm_budget_gb": 96, "short_lane_sms": 4,
         "served": s_stats, "served_one_lane": o_stats, "plain": p_stats,
+        "p99_ms": {"served": s_stats["p99_ms"], "served_one_lane": o_stats["p99_ms"],
+                   "plain": p_stats["p99_ms"]},
+        "p50_ms": {"served": s_stats["p50_ms"], "served_one_lane": o_stats["p50_ms"],
+                   "plain": p_stats["p50_ms"]},
         "burst": {"served": sb_stats, "plain": pb_stats,
                   "served_vs_plain_throughput": sb_stats["throughput"] / pb_stats["throughput"]},
-        "results_equal_alone_vs_mix": same,
-        "clocks": clocks,
+        "results_equal_alone_vs_mix": bool(same),
+        "clocks": clocks, "clocks_plain": p_clocks,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    return 0
+    if jobs is not None:
+        probes = [r for r in served if r.work.name.startswith("probe")][:8]
+        inst = []
+        for r in served:
+            if not r.work.name.startswith("probe") and all(r.work.name != q.work.name
+                                                            for q in inst):
+                inst.append(r)
+            if len(inst) == 2:
+                break
+
+        def parity():
+            import oracle.oracle as orc
+            errs = []
+            for r in probes:
+                o0, oh, init = orc.run(r.work, n_threads=1)
+                errs.append(float(abs(r.R[0] - orc.reflectivity(init, o0, oh)[0][0])))
+            ierr = []
+            for r in inst:
+                chs = [0, r.work.n_ch - 1]
+                o0, oh, init = orc.run(r.work, channels=chs, n_threads=min(2, jobs.threads))
+                oR = orc.reflectivity(init, o0, oh)[0]
+                ierr.append(float(np.max(np.abs(r.R[chs] - oR))))
+            return {"vs": "FP64 oracle", "probes": len(probes),
+                    "max_abs_err_R_probes": max(errs) if errs else None,
+                    "instances": [r.work.name for r in inst], "channels_per_instance": 2,
+                    "max_abs_err_R_instances": max(ierr) if ierr else None,
+                    "tolerance_R": TOL_R,
+                    "note": "R_i of requests served in the mix (first served form)"}
+
+        jobs.submit("served", parity)
+    return out
 
 
+# --------------------------------------------------------------------------- config 2
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -462,6 +643,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="N = 1: skip the nested batched / served / 3d objects")
+    ap.add_argument("--extra-steps", type=int, default=5,
+                    help="timed passes of the batched and 3d sections (at most --steps)")
     ap.add_argument("--channels", type=int, default=1024,
                     help="channels of the deformed workload (profiling: a smaller instance)")
     ap.add_argument("--nz", type=int, default=2000, help="z steps of the deformed workload")
@@ -472,29 +657,30 @@ def main():
     ap.add_argument("--split-order", type=int, default=1, choices=[1, 2, 4],
                     help="operator splitting of the deformed workload (Eq. split-op)")
     ap.add_argument("--workload", default="deformed", choices=["deformed", "batched", "served", "3d"],
-                    help="deformed: one instance (default line); batched: 64 uneven instances "
-                         "in one work-queue launch vs one launch per instance")
+                    help="deformed: one instance (default line); batched / served / 3d: that "
+                         "section alone, as its own line")
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--requests", type=int, default=10000,
                     help="served: number of requests (80 % rocking-curve probes)")
     ap.add_argument("--load", type=float, default=0.7, help="served: offered load / capacity")
+    ap.add_argument("--independent", action="store_true",
+                    help="N > 1: every rank marches its own instance (weak scaling) instead of "
+                         "the ranks splitting one instance's channels")
     ap.add_argument("--shard-channels", action="store_true",
-                    help="deformed workload: the ranks split ONE instance's channels and "
-                         "sum-reduce its time response (strong scaling) instead of each "
-                         "marching its own instance")
+                    help="split one instance's channels across the ranks (the default at N > 1)")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, world, rank)
-    if args.workload == "batched":
-        return run_batched(args, world, rank, local)
-    if args.workload == "served":
-        return run_served(args, world, rank, local)
-    if args.workload == "3d":
-        return run_3d(args, world, rank, local)
+    single = {"batched": run_batched, "served": run_served, "3d": run_3d}
+    if args.workload in single:
+        obj = single[args.workload](args, world, rank, local)
+        if rank == 0:
+            print(json.dumps({"n_gpus": world, "data": "synthetic", **obj}), flush=True)
+        return 0
 
     import torch
-    from paper_2201_08500_gb300 import bpm
+    from paper_2201_08500_gb300 import bpm, shard
 
     torch.cuda.set_device(local)
     dist = None
@@ -507,22 +693,18 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    from paper_2201_08500_gb300 import shard
-    w_all = None  # the sharded instance (--shard-channels)
-    if args.shard_channels:
-        w_all = workloads.deformed(n_ch=args.channels, nx=args.nx, nz=args.nz, seed=2)
-        first, cnt = shard.channel_blocks(w_all.n_ch, world)[rank]
-        if cnt == 0:
-            raise SystemExit("--shard-channels needs at least one channel per rank")
-        w = w_all.subset(list(range(first, first + cnt)))
+    peaks = measure_cuda_core_peaks(local)
+    sharded = world > 1 and not args.independent
+    w_all = None  # the sharded instance
+    if sharded:
+        w, w_all, first = rank_share(args.channels, args.nx, args.nz, world, rank)
     else:
         w = rank_workload(args.channels, args.nx, args.nz, rank)
     w.split_order = args.split_order
     stream = torch.cuda.current_stream()
     u_dev = torch.from_numpy(np.ascontiguousarray(w.u)).cuda()
-    # launch form chosen by the autotuner (untimed setup)
-    # (256 steps: short runs over-weight the one-time per-channel table copy of
-    # the shared-memory form)
+    # launch form chosen by the autotuner (untimed setup); 256 steps: short runs
+    # over-weight the one-time per-channel table copy of the shared-memory form
     tried = []
     if args.launch_form is None:
         _, tried = bpm.tune(w.dims, w.nx, w.ny, w.dx, w.dy, w.dz, w.n_ch,
@@ -530,7 +712,7 @@ def main():
     plan = bpm.Plan(w.dims, w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.n_ch, stream=stream,
                     zassenhaus=w.zassenhaus, split_order=w.split_order)
     plan.set_timing(True)
-    if w_all is not None:
+    if sharded:
         plan.set_channel_shard(first, w_all.n_ch, shard.pulse_spacing(w_all.omega))
         t_dev = torch.empty((w_all.n_ch, w.plane), dtype=torch.complex128, device="cuda")
     if args.launch_form is not None:
@@ -538,16 +720,18 @@ def main():
                         channels_per_block=1 if args.launch_form >= 2 else None)
     omega = np.ascontiguousarray(w.omega)
     S = np.ascontiguousarray(w.S)
+    rows = {}
 
     def step(u):
         plan.set_crystal(w.chi0, w.chih, w.chihb, w.theta_B, w.lambda_B, w.x_surface,
                          w.thickness, u=u)
         plan.set_pulse(omega, S, w.theta_i, w.x0, w.w0, w.zx, w.zR)
         plan.run()
-        if w_all is not None and world > 1:
-            # the one exchange of a sharded pulse: sum the time-response parts
+        if sharded:
+            # the one exchange of a sharded pulse: reduce-scatter the time
+            # response over t (each rank keeps its block of time rows)
             plan.fetch(bpm.BPM_FIELD_EH_TIME, out=t_dev)
-            shard.combine(t_dev, 0.0)
+            rows["t"], rows["first"], _ = shard.combine_scatter(t_dev, 0.0)
 
     # L2 (129 MB) is flushed between timed steps by writing a 256 MB buffer
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
@@ -556,8 +740,7 @@ def main():
         step(u_dev)
     barrier()
 
-    sampler = ClockSampler(local)
-    sampler.start()
+    sampler = ClockSampler(local).start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     march_ms = []
@@ -576,27 +759,30 @@ def main():
     ms = max_over_ranks(ms_local, dist, device="cuda")
     cells_per_rank = w.cell_updates
     # whole-job cell-updates: every rank's instance, or the one sharded instance
-    job_cells = w_all.cell_updates if w_all is not None else world * cells_per_rank
+    job_cells = w_all.cell_updates if sharded else world * cells_per_rank
     value = whole_job_value(1, job_cells, ms)
 
     # end to end through the C ABI with host buffers: pinned u in, R and the
-    # time response out, copies inside the timed region
+    # time response (this rank's rows of it when sharded) out, copies inside
+    # the timed region
     u_pin = torch.from_numpy(np.ascontiguousarray(w.u)).pin_memory()
-    t_rows = w_all.n_ch if w_all is not None else w.n_ch
+    t_rows = w.n_ch
+    if sharded:
+        t_rows = rows["t"].shape[0]
     t_host = torch.empty((t_rows, w.plane), dtype=torch.complex128).pin_memory()
     R = np.empty(w.n_ch)
     e2e_ms = []
     for i in range(max(2, min(args.steps, 5))):
-        torch.cuda.synchronize()
+        barrier()
         t0 = time.perf_counter()
         step(u_pin)
-        if w_all is not None and world > 1:
-            t_host.copy_(t_dev)  # the reduced time response
+        if sharded:
+            t_host.copy_(rows["t"])
         else:
             plan.fetch(bpm.BPM_FIELD_EH_TIME, out=t_host)
         R, _, _ = plan.reflectivity()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e = statistics.median(e2e_ms)
+    e2e = max_over_ranks(statistics.median(e2e_ms), dist, device="cuda")
     h2d = w.u.nbytes + omega.nbytes + S.nbytes
     d2h = t_host.numel() * t_host.element_size() + 2 * R.nbytes
 
@@ -613,35 +799,48 @@ def main():
     props = torch.cuda.get_device_properties(local)
     pk = measured_peaks()
     sm_max = pk.get("sm_max_mhz", 2070.0)
-    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    peak_units = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    peak = peaks["fp32"]["tflops"]
+    executed = EXECUTED_FLOPS.get(kernel) if w.split_order == 1 else None
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "strong" if w_all is not None else "weak",
+            "higher_is_better": True, "scaling": "strong" if sharded else "weak",
             "vs_baseline": None,
             "dtype": "c64 fields / f32 butterflies (f64 setup and time sum)",
             "data": "synthetic",
-            "config": {"workload": w.name, "nx": w.nx, "nz": w.nz,
-                       "channels": w_all.n_ch if w_all is not None else w.n_ch,
+            "config": {"workload": w_all.name if sharded else w.name, "nx": w.nx, "nz": w.nz,
+                       "channels": w_all.n_ch if sharded else w.n_ch,
                        "split_order": w.split_order,
                        "crystal": "thermal bump u = A exp(-x'^2/w^2)(z/Z)^2",
                        "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": (f"{world} x channel shard of one instance, time "
-                                       f"response sum-reduced" if w_all is not None
+                                       f"response reduce-scattered over t" if sharded
                                        else f"{world} x independent instance"),
                        "launch": plan.launch(), "tuned": tried},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak,
+                         "peak_basis": "measured FP32 FFMA rate on every SM (peaks.fp32, "
+                                       "bpm_measure_peak)",
+                         "peak_unit_count": peak_units,
+                         "frac_unit_count": achieved / peak_units,
+                         "unit_count_basis": f"{props.multi_processor_count} SMs x 128 FP32 "
+                                             f"lanes x 2 x {sm_max:.0f} MHz",
+                         "flops_per_cell_update": flops_per_cell(n, w.split_order),
+                         "flops_basis": "nominal: 4 FFTs at 5 N log2 N + 12 + 40 per cell-update",
+                         "executed_flops_per_cell_update": executed,
+                         "frac_executed": (None if executed is None else
+                                           cells_per_rank * executed / (march_avg * 1e-3)
+                                           / 1e12 / peak),
+                         "executed_basis": "ncu FADD + FMUL + 2 FFMA thread instructions of "
+                                           "this kernel per cell-update",
                          # the captured launch held the whole instance
                          "traffic": (MEASURED_TRAFFIC.get((kernel, w.name, w.split_order))
-                                     if w_all is None or world == 1 else None),
+                                     if not sharded else None),
                          "algorithmic_bytes": alg_bytes,
-                         "kernel": kernel,
-                         "flops_per_cell_update": flops_per_cell(n, w.split_order),
-                         "march_ms": march_avg,
-                         "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 "
-                                       f"x {sm_max:.0f} MHz"},
+                         "kernel": kernel, "march_ms": march_avg},
+            "peaks": peaks,
             "e2e": {"value": job_cells / (e2e * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": 5 * args.steps,
@@ -663,10 +862,29 @@ def main():
             line["parity"] = {"vs": "FP64 oracle", "channels": int(n_s),
                               "max_err_per_channel": float(err.max()),
                               "median_err_per_channel": float(np.median(err)),
+                              "rel_l2_e0": float(np.linalg.norm(g0 - o0) / np.linalg.norm(o0)),
                               "rel_l2_eh": float(np.linalg.norm(gh - oh) / np.linalg.norm(oh)),
-                              "tolerance": 1e-4}
-        print(json.dumps(line), flush=True)
+                              "tolerance": TOL_FIELD}
     plan.close()
+    del u_dev, flush
+    if world == 1 and not args.no_extras:
+        torch.cuda.empty_cache()
+        jobs = OracleJobs(threads=max(1, (os.cpu_count() or 2) - 4))
+        extras = {}
+        t_x = time.perf_counter()
+        extras["batched"] = run_batched(args, world, rank, local, jobs)
+        torch.cuda.empty_cache()
+        extras["3d"] = run_3d(args, world, rank, local, jobs)
+        torch.cuda.empty_cache()
+        extras["served"] = run_served(args, world, rank, local, jobs)
+        for name in ("batched", "3d", "served"):
+            extras[name]["parity"] = jobs.result(name)
+        jobs.close()
+        line.update(extras)
+        line["extras_wall_s"] = time.perf_counter() - t_x
+        line["gpu_launches_extras"] = {k: extras[k].get("gpu_launches") for k in extras}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     return 0

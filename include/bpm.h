@@ -383,14 +383,29 @@ BPM_API const char* bpm_batch_last_error(bpm_batch b);
 BPM_API void bpm_batch_destroy(bpm_batch b);
 
 /* ---------------------------------------------------------------------------
+ * Measured CUDA-core peak (no counterpart in the paper: the denominator of the
+ * march kernels' rooflines).  One launch of independent fused multiply-add
+ * chains on every SM: kind BPM_PEAK_FP32 (FFMA) or BPM_PEAK_FP64 (DFMA),
+ * `iters` loop trips of 128 FMAs per thread (1024 threads per SM).  Writes the
+ * achieved rate in flop/s (an FMA counts 2) and the launch's duration by CUDA
+ * events on cuda_stream, and waits for the launch.  Allocates nothing.
+ * Returns BPM_ERR_INVALID_ARG for a null output, iters < 1 or an unknown
+ * kind, BPM_ERR_UNSUPPORTED without a GB300, BPM_ERR_CUDA if the launch fails.
+ * ------------------------------------------------------------------------- */
+#define BPM_PEAK_FP32 0
+#define BPM_PEAK_FP64 1
+BPM_API bpm_status bpm_measure_peak(int kind, int iters, double* flop_per_s, float* ms,
+                                    void* cuda_stream);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free single-instance run.  The paper has no counterpart: this is
  * a deployment convenience of this library.
  *
  * For callers that cannot allocate device memory while they run this code:
- * work being recorded into a CUDA graph (cudaMalloc is not a stream operation
- * and cannot be captured), processes whose device memory is wholly handed out
- * by their own pool, and latency-bound loops that must not take the
- * allocator's lock.  The caller passes the inputs and outputs; every
+ * processes whose device memory is wholly handed out by their own pool (a
+ * cudaMalloc there fails or steals memory the pool has promised elsewhere),
+ * and latency-bound loops that must not take the allocator's lock or risk
+ * fragmenting the heap.  The caller passes the inputs and outputs; every
  * intermediate buffer (deformation factor, propagator tables, coupling
  * coefficients, FFT constants, norms) lives in one fixed device array inside
  * the library (bpm_noalloc_scratch_bytes(), 6.3 MB), which every GPU that
@@ -406,7 +421,12 @@ BPM_API void bpm_batch_destroy(bpm_batch b);
  * [n_channels][nx]), reflectivities R_i into refl_dev (device float64
  * [n_channels]).  u_field_dev is a device float64 [nz][nx] displacement or
  * NULL (perfect crystal); omega and weight_re_im are host arrays as for
- * bpm_set_pulse.  Asynchronous on cuda_stream.
+ * bpm_set_pulse.  Asynchronous on cuda_stream, except that omega,
+ * weight_re_im and the FFT constants are copied into the array with
+ * cudaMemcpyAsync from pageable host memory, so those copies are staged by
+ * the driver before the call returns.  The call takes no sizes for the
+ * caller's buffers: they must hold at least the sizes above (the Python
+ * binding checks them).
  *
  * The first call on a device looks up the array's device address (with that
  * device current); make that first call before any stream capture.  All calls

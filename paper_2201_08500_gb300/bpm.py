@@ -30,7 +30,7 @@ EXPORTS = ("bpm_plan_create", "bpm_set_crystal", "bpm_set_pulse", "bpm_set_field
            "bpm_set_geometry", "bpm_batch_set_max_blocks", "bpm_batch_pending",
            "bpm_batch_graph_kernels", "bpm_get_launch", "bpm_set_launch", "bpm_tune",
            "bpm_tune_save", "bpm_tune_load", "bpm_tune_clear", "bpm_set_channel_shard",
-           "bpm_set_crystal_shape")
+           "bpm_set_crystal_shape", "bpm_measure_peak")
 
 
 class BpmError(RuntimeError):
@@ -116,6 +116,8 @@ def load(path: str = LIB_PATH):
         "bpm_plan_destroy": ([_P], None),
         "bpm_version": ([], ctypes.c_char_p),
         "bpm_plan_bytes": ([ctypes.POINTER(Grid), _I, _I], ctypes.c_size_t),
+        "bpm_measure_peak": ([_I, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_float), _P],
+                             _I),
         "bpm_batch_create": ([ctypes.c_size_t, _P, ctypes.POINTER(_P)], _I),
         "bpm_batch_submit": ([_P, _P, ctypes.POINTER(ctypes.c_uint64)], _I),
         "bpm_batch_step": ([_P, _I], _I),
@@ -480,7 +482,28 @@ def run_noalloc(w, e0_out, eh_out, refl_out, u_dev=None, stream=None):
 
     e0_out, eh_out: device complex64 [n_ch, nx]; refl_out: device float64 [n_ch];
     u_dev: device float64 [nz, nx] displacement or None.  For callers that must
-    not allocate device memory while they run (see include/bpm.h)."""
+    not allocate device memory while they run (see include/bpm.h).
+
+    The C call takes no buffer sizes, so every tensor is checked here (CUDA,
+    dtype, contiguous, element count) and a mismatch raises BpmError
+    (INVALID_ARG) before anything is launched."""
+    import torch
+    n_ch, nx, nz = int(w.n_ch), int(w.nx), int(w.nz)
+
+    def need(name, t, dtype, numel):
+        ok = (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype
+              and t.is_contiguous() and t.numel() == numel)
+        if not ok:
+            got = (f"{t.device} {t.dtype} {tuple(t.shape)} contiguous={t.is_contiguous()}"
+                   if isinstance(t, torch.Tensor) else type(t).__name__)
+            raise BpmError(1, f"run_noalloc: {name} must be a contiguous CUDA {dtype} tensor of "
+                              f"{numel} elements, got {got}")
+
+    need("e0_out", e0_out, torch.complex64, n_ch * nx)
+    need("eh_out", eh_out, torch.complex64, n_ch * nx)
+    need("refl_out", refl_out, torch.float64, n_ch)
+    if u_dev is not None:
+        need("u_dev", u_dev, torch.float64, nz * nx)
     L = load()
     g = Grid(2, int(w.nx), 1, int(w.nz), float(w.dx), 0.0, float(w.dz), 1, int(w.zassenhaus))
     chi0, chih, chihb = complex(w.chi0), complex(w.chih), complex(w.chihb)
@@ -494,3 +517,17 @@ def run_noalloc(w, e0_out, eh_out, refl_out, u_dev=None, stream=None):
                            _ptr(refl_out), _stream_handle(stream))
     if st != 0:
         raise BpmError(st, L.bpm_noalloc_last_error().decode())
+
+
+BPM_PEAK_FP32, BPM_PEAK_FP64 = 0, 1
+
+
+def measure_peak(kind: int = BPM_PEAK_FP32, iters: int = 1 << 16, stream=None):
+    """One launch of FMA chains on every SM (bpm_measure_peak): (flop/s, ms)."""
+    L = load()
+    rate, ms = ctypes.c_double(), ctypes.c_float()
+    st = L.bpm_measure_peak(int(kind), int(iters), ctypes.byref(rate), ctypes.byref(ms),
+                            _stream_handle(stream))
+    if st != 0:
+        raise BpmError(st, "bpm_measure_peak failed")
+    return rate.value, ms.value

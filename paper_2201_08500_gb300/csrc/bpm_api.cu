@@ -405,6 +405,7 @@ BPM_API const char* bpm_last_error(bpm_plan plan) {
 
 BPM_API bpm_status bpm_plan_create(const bpm_grid* grid, int n_channels, void* cuda_stream,
                                    bpm_plan* out) {
+  BPM_NVTX();
   if (!grid || !out) return fail(nullptr, BPM_ERR_INVALID_ARG, "null grid or output pointer");
   *out = nullptr;
   const bpm_grid& g = *grid;
@@ -551,6 +552,7 @@ BPM_API bpm_status bpm_set_crystal(bpm_plan p, double chi0_re, double chi0_im, d
                                    double chih_im, double chihbar_re, double chihbar_im,
                                    double theta_B, double lambda_B, double x_surface,
                                    double thickness, const double* u_field, int u_on_device) {
+  BPM_NVTX();
   if (!p) return fail(nullptr, BPM_ERR_INVALID_ARG, "null plan");
   if (!(theta_B >= 0.0) || theta_B >= 85.0 * kPiHost / 180.0)
     return fail(p, BPM_ERR_INVALID_ARG, "theta_B must lie in [0, 85) degrees");
@@ -607,6 +609,7 @@ BPM_API bpm_status bpm_set_crystal(bpm_plan p, double chi0_re, double chi0_im, d
 }
 
 BPM_API bpm_status bpm_set_geometry(bpm_plan p, double tan_psi, double z_begin, double z_end) {
+  BPM_NVTX();
   if (!p) return fail(nullptr, BPM_ERR_INVALID_ARG, "null plan");
   if (!(std::fabs(tan_psi) < 1e3) || !(z_begin < z_end))
     return fail(p, BPM_ERR_INVALID_ARG, "need |tan_psi| < 1e3 and z_begin < z_end");
@@ -619,6 +622,7 @@ BPM_API bpm_status bpm_set_geometry(bpm_plan p, double tan_psi, double z_begin, 
 }
 
 BPM_API bpm_status bpm_set_crystal_shape(bpm_plan p, const unsigned char* mask, int on_device) {
+  BPM_NVTX();
   if (!p) return fail(nullptr, BPM_ERR_INVALID_ARG, "null plan");
   if (!mask) {
     p->sa.mask = nullptr;  // back to the crystal's boundaries (the copy is kept for reuse)
@@ -641,6 +645,7 @@ BPM_API bpm_status bpm_set_crystal_shape(bpm_plan p, const unsigned char* mask, 
 
 BPM_API bpm_status bpm_set_pulse(bpm_plan p, const double* omega, const double* weight_re_im,
                                  double theta_i, double x0, double w0, double zx, double zR) {
+  BPM_NVTX();
   if (!p) return fail(nullptr, BPM_ERR_INVALID_ARG, "null plan");
   if (!omega || !weight_re_im) return fail(p, BPM_ERR_INVALID_ARG, "null omega or weights");
   if (!p->have_crystal) return fail(p, BPM_ERR_STATE, "bpm_set_crystal must come first");
@@ -689,6 +694,7 @@ BPM_API bpm_status bpm_set_pulse(bpm_plan p, const double* omega, const double* 
 }
 
 BPM_API bpm_status bpm_set_channel_shard(bpm_plan p, int first, int n_total, double d_omega) {
+  BPM_NVTX();
   if (!p) return fail(nullptr, BPM_ERR_INVALID_ARG, "null plan");
   if (first < 0 || n_total < p->n_ch || first + p->n_ch > n_total)
     return fail(p, BPM_ERR_INVALID_ARG, "shard must lie within [0, n_total)");
@@ -713,6 +719,7 @@ BPM_API bpm_status bpm_set_channel_shard(bpm_plan p, int first, int n_total, dou
 
 BPM_API bpm_status bpm_set_fields(bpm_plan p, const void* e0, const void* eh, int z_step,
                                   int on_device) {
+  BPM_NVTX();
   if (!p) return fail(nullptr, BPM_ERR_INVALID_ARG, "null plan");
   if (!e0 || !eh) return fail(p, BPM_ERR_INVALID_ARG, "null field pointer");
   if (!p->have_pulse) return fail(p, BPM_ERR_STATE, "bpm_set_pulse must come first");
@@ -728,6 +735,7 @@ BPM_API bpm_status bpm_set_fields(bpm_plan p, const void* e0, const void* eh, in
 }
 
 BPM_API bpm_status bpm_run(bpm_plan p, int n_steps) {
+  BPM_NVTX();
   if (!p) return fail(nullptr, BPM_ERR_INVALID_ARG, "null plan");
   if (!p->have_pulse) return fail(p, BPM_ERR_STATE, "bpm_set_pulse must come first");
   if (n_steps < 0 || p->z + n_steps > p->grid.nz)
@@ -807,6 +815,7 @@ BPM_API bpm_status bpm_run(bpm_plan p, int n_steps) {
 }
 
 BPM_API bpm_status bpm_set_stream(bpm_plan p, void* cuda_stream) {
+  BPM_NVTX();
   if (!p) return fail(nullptr, BPM_ERR_INVALID_ARG, "null plan");
   cudaStream_t ns = static_cast<cudaStream_t>(cuda_stream);
   if (ns == p->stream) return BPM_OK;
@@ -821,6 +830,7 @@ BPM_API bpm_status bpm_set_stream(bpm_plan p, void* cuda_stream) {
 }
 
 BPM_API bpm_status bpm_sync(bpm_plan p) {
+  BPM_NVTX();
   if (!p) return fail(nullptr, BPM_ERR_INVALID_ARG, "null plan");
   BPM_CUDA(p, cudaStreamSynchronize(p->stream), "stream synchronize");
   return BPM_OK;
@@ -828,6 +838,7 @@ BPM_API bpm_status bpm_sync(bpm_plan p) {
 
 BPM_API bpm_status bpm_fetch_fields(bpm_plan p, int which, void* dst, size_t bytes,
                                     int dst_on_device) {
+  BPM_NVTX();
   if (!p) return fail(nullptr, BPM_ERR_INVALID_ARG, "null plan");
   if (!dst) return fail(p, BPM_ERR_INVALID_ARG, "null destination");
   const size_t n = size_t(p->n_ch) * p->plane;
@@ -853,6 +864,7 @@ BPM_API bpm_status bpm_fetch_fields(bpm_plan p, int which, void* dst, size_t byt
 }
 
 BPM_API bpm_status bpm_fetch_reflectivity(bpm_plan p, double* R, double* T, double* R_int) {
+  BPM_NVTX();
   if (!p) return fail(nullptr, BPM_ERR_INVALID_ARG, "null plan");
   if (!p->have_pulse) return fail(p, BPM_ERR_STATE, "no pulse set");
   std::vector<double> r(p->n_ch), t(p->n_ch);
@@ -906,6 +918,7 @@ BPM_API bpm_status bpm_get_launch(bpm_plan p, bpm_launch* out) {
 }
 
 BPM_API bpm_status bpm_set_launch(bpm_plan p, const bpm_launch* f) {
+  BPM_NVTX();
   if (!p || !f) return fail(p, BPM_ERR_INVALID_ARG, "null argument");
   if (!launch_valid(p->grid, f->form, f->channels_per_block, f->row_threads))
     return fail(p, BPM_ERR_INVALID_ARG, "launch form not available for this plan");
@@ -950,6 +963,7 @@ bpm_status time_form(bpm_plan p, int steps, cudaEvent_t e0, cudaEvent_t e1, floa
 
 BPM_API bpm_status bpm_tune(const bpm_grid* grid, int n_channels, int steps, bpm_launch* best,
                             bpm_launch* all, int max_all, int* n_all) {
+  BPM_NVTX();
   if (!grid || !best || n_channels < 1 || steps < 1 || (all && max_all < 0))
     return fail(nullptr, BPM_ERR_INVALID_ARG, "bpm_tune: bad arguments");
   bpm_grid g = *grid;
@@ -1022,6 +1036,7 @@ BPM_API bpm_status bpm_tune(const bpm_grid* grid, int n_channels, int steps, bpm
 }
 
 BPM_API bpm_status bpm_tune_save(const char* path) {
+  BPM_NVTX();
   if (!path) return fail(nullptr, BPM_ERR_INVALID_ARG, "null path");
   FILE* f = std::fopen(path, "w");
   if (!f) return fail(nullptr, BPM_ERR_INVALID_ARG, std::string("cannot write ") + path);
@@ -1041,6 +1056,7 @@ BPM_API bpm_status bpm_tune_save(const char* path) {
 }
 
 BPM_API bpm_status bpm_tune_load(const char* path, int* n_loaded) {
+  BPM_NVTX();
   if (!path) return fail(nullptr, BPM_ERR_INVALID_ARG, "null path");
   FILE* f = std::fopen(path, "r");
   if (!f) return fail(nullptr, BPM_ERR_INVALID_ARG, std::string("cannot read ") + path);
@@ -1089,6 +1105,7 @@ BPM_API void bpm_tune_clear(void) {
 }
 
 BPM_API void bpm_plan_destroy(bpm_plan p) {
+  BPM_NVTX();
   if (!p) return;
   cudaStreamSynchronize(p->stream);
   free_plan_buffers(p);
@@ -1250,8 +1267,16 @@ bpm_status enqueue_round(bpm_batch b, RoundSlot& r, int chunk) {
       tmp.push_back(t);
     }
   }
-  std::stable_sort(tmp.begin(), tmp.end(), [](const Tmp& x, const Tmp& y) {
-    return x.q != y.q ? x.q < y.q : x.cost > y.cost;
+  // launch rank of each queue: the longest items (Nx = 8192, every order) first,
+  // then 4096, 2048 and 1024, then the resident small-N queues
+  static constexpr int kOrder[kQueueCount] = {
+      kQueueTm8192,   kQueueTm8192s2, kQueueBig4,     kQueueTm4096,   kQueueTm4096s2,
+      kQueuePk4096s4, kQueueTm2048,   kQueueTm2048s2, kQueuePk2048s4, kQueuePk1024s4,
+      kQueueSmall,    kQueueSmall2,   kQueueSmall4};
+  int rank[kQueueCount];
+  for (int i = 0; i < kQueueCount; ++i) rank[kOrder[i]] = i;
+  std::stable_sort(tmp.begin(), tmp.end(), [&rank](const Tmp& x, const Tmp& y) {
+    return x.q != y.q ? rank[x.q] < rank[y.q] : x.cost > y.cost;
   });
   int cnt[kQueueCount] = {};
   for (auto& t : tmp) cnt[t.q]++;
@@ -1271,7 +1296,8 @@ bpm_status enqueue_round(bpm_batch b, RoundSlot& r, int chunk) {
   // blocks per SM: the Nx = 8192 items (the longest) first, then the smaller
   // ones; the idle tail is one item per queue.
   int off = 0;
-  for (int q = 0; q < kQueueCount; ++q) {
+  for (int i = 0; i < kQueueCount; ++i) {
+    const int q = kOrder[i];
     if (cnt[q] > 0)
       BPM_BCUDA(b, launch_batch(r.d_plans, r.d_items + off, cnt[q], r.d_counter + q, q,
                                 std::min(cnt[q], sms * batch_blocks_per_sm(q)), b->stream),
@@ -1315,6 +1341,7 @@ BPM_API size_t bpm_plan_bytes(const bpm_grid* grid, int n_channels, int host_u) 
 }
 
 BPM_API bpm_status bpm_batch_create(size_t hbm_budget_bytes, void* cuda_stream, bpm_batch* out) {
+  BPM_NVTX();
   if (!out) return bfail(nullptr, BPM_ERR_INVALID_ARG, "null output");
   *out = nullptr;
   const DeviceInfo& di = device_info();
@@ -1332,6 +1359,7 @@ BPM_API bpm_status bpm_batch_create(size_t hbm_budget_bytes, void* cuda_stream, 
 }
 
 BPM_API bpm_status bpm_batch_submit(bpm_batch b, bpm_plan p, uint64_t* ticket) {
+  BPM_NVTX();
   if (!b || !p || !ticket) return bfail(b, BPM_ERR_INVALID_ARG, "null argument");
   if (!p->have_pulse) return bfail(b, BPM_ERR_STATE, "plan needs crystal and pulse first");
   if (p->grid.dims != 2) return bfail(b, BPM_ERR_UNSUPPORTED, "batches take 2D plans");
@@ -1359,6 +1387,7 @@ BPM_API bpm_status bpm_batch_submit(bpm_batch b, bpm_plan p, uint64_t* ticket) {
 }
 
 BPM_API bpm_status bpm_batch_step(bpm_batch b, int chunk_steps) {
+  BPM_NVTX();
   if (!b) return bfail(nullptr, BPM_ERR_INVALID_ARG, "null batch");
   if (chunk_steps < 1) return bfail(b, BPM_ERR_INVALID_ARG, "chunk_steps must be >= 1");
   RoundSlot& r = b->slots[b->next_slot];
@@ -1369,6 +1398,7 @@ BPM_API bpm_status bpm_batch_step(bpm_batch b, int chunk_steps) {
 BPM_API bpm_status bpm_batch_run(bpm_batch b) { return bpm_batch_step(b, 1 << 30); }
 
 BPM_API bpm_status bpm_batch_poll(bpm_batch b, uint64_t ticket, int* done) {
+  BPM_NVTX();
   if (!b || !done) return bfail(b, BPM_ERR_INVALID_ARG, "null argument");
   *done = 0;
   auto f = b->finished.find(ticket);
@@ -1398,6 +1428,7 @@ BPM_API bpm_status bpm_batch_poll(bpm_batch b, uint64_t ticket, int* done) {
 }
 
 BPM_API bpm_status bpm_batch_cancel(bpm_batch b, uint64_t ticket) {
+  BPM_NVTX();
   if (!b) return bfail(nullptr, BPM_ERR_INVALID_ARG, "null batch");
   for (size_t i = 0; i < b->entries.size(); ++i) {
     BatchEntry& e = b->entries[i];
@@ -1417,6 +1448,7 @@ BPM_API bpm_status bpm_batch_cancel(bpm_batch b, uint64_t ticket) {
 }
 
 BPM_API bpm_status bpm_batch_sync(bpm_batch b) {
+  BPM_NVTX();
   if (!b) return bfail(nullptr, BPM_ERR_INVALID_ARG, "null batch");
   BPM_BCUDA(b, cudaStreamSynchronize(b->stream), "batch synchronize");
   return BPM_OK;
@@ -1427,6 +1459,7 @@ BPM_API bpm_status bpm_batch_sync(bpm_batch b) {
 // round to nz, time response.  The graph is captured on the first call and
 // again whenever the set of entries changes.
 BPM_API bpm_status bpm_batch_run_graph(bpm_batch b) {
+  BPM_NVTX();
   if (!b) return bfail(nullptr, BPM_ERR_INVALID_ARG, "null batch");
   uint64_t key = 1469598103934665603ull;
   for (const auto& e : b->entries) key = (key ^ reinterpret_cast<uintptr_t>(e.plan)) * 1099511628211ull;
@@ -1539,6 +1572,7 @@ BPM_API const char* bpm_batch_last_error(bpm_batch b) {
 }
 
 BPM_API void bpm_batch_destroy(bpm_batch b) {
+  BPM_NVTX();
   if (!b) return;
   cudaStreamSynchronize(b->stream);
   if (b->side) cudaStreamSynchronize(b->side);

@@ -3,9 +3,20 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 namespace bpm {
+
+// One NVTX range per C-ABI call, named after the call (header-only NVTX 3: a
+// no-op unless a profiler or tracing tool is attached to the process).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define BPM_NVTX() ::bpm::NvtxRange bpm_nvtx_range_(__func__)
 
 // Number of complex elements each thread holds per envelope in the resident
 // march kernel: one radix-16 butterfly group per thread per stage.
@@ -78,8 +89,10 @@ struct BatchItem {
   int reserved;
 };
 
-// Work-queue launchers (bpm_batch.cu).  A round sorts its items into queues,
-// launched back to back in this order (longest items first within each):
+// Work-queue launchers (bpm_batch.cu).  A round sorts its items into these
+// queues (longest items first within each) and launches the queues back to
+// back, the Nx = 8192 queues of every order first, then 4096, 2048, 1024 and
+// the resident small-N queues (enqueue_round in bpm_api.cu):
 enum BatchQueue {
   kQueueTm8192 = 0,  // first order, Nx = 8192: parked form, TMEM tables
   kQueueTm4096,      // first order, Nx = 4096: parked form, TMEM tables, 2 blocks / SM

@@ -2,9 +2,9 @@
 // intermediate buffers in a fixed, file-scope device array.
 //
 // Why: some callers cannot call cudaMalloc while they run this code -- for
-// example code that runs inside a CUDA graph being captured, a process whose
-// device memory is entirely handed out by a caller-side pool, or a real-time
-// loop that must not take the allocator's lock or risk fragmentation.  They
+// example a process whose device memory is entirely handed out by a
+// caller-side pool, or a real-time loop that must not take the allocator's
+// lock or risk fragmentation.  They
 // pass their own input and output buffers; everything else (the deformation
 // factor, the propagator tables, the coupling coefficients, the FFT constants,
 // per-channel norms) lives in g_static_scratch below.
@@ -103,6 +103,7 @@ BPM_API bpm_status bpm_run_noalloc(const bpm_grid* grid, int n_channels,
                                    const double* omega, const double* weight_re_im,
                                    const bpm_beam_params* beam, void* e0_dev, void* eh_dev,
                                    double* refl_dev, void* cuda_stream) {
+  BPM_NVTX();
   if (!grid || !crystal || !beam || !omega || !weight_re_im || !e0_dev || !eh_dev || !refl_dev)
     return sfail(BPM_ERR_INVALID_ARG, "null argument");
   const bpm_grid& g = *grid;

@@ -8,7 +8,9 @@ psi_h(t_j, x) (Section 3.3) and the integrated reflectivity R_int
 - bpm_set_channel_shard makes that plan's time response and R_int this
   block's parts of the two sums, with the global channel indices in the phase
   factors;
-- one sum-reduce over the process group combines the parts.
+- one sum-reduce over the process group combines the parts: combine()
+  leaves the whole sum on every rank (an all-reduce), combine_scatter() a
+  block of time rows on each (a reduce-scatter over t, half the traffic).
 
 The per-channel R_i need no reduce: each rank holds its own block's values.
 """
@@ -51,6 +53,43 @@ def combine(time_part, r_int_part: float, group=None):
     r = torch.tensor([float(r_int_part)], dtype=torch.float64, device=time_part.device)
     dist.all_reduce(r, op=dist.ReduceOp.SUM, group=group)
     return float(r.item())
+
+
+def time_row_blocks(n_time: int, world: int) -> list[tuple[int, int]]:
+    """Rows of the time response each rank holds after combine_scatter: equal
+    blocks of ceil(n_time / world) rows (the last ones shorter or empty)."""
+    if n_time < 1 or world < 1:
+        raise ValueError("n_time and world must be >= 1")
+    per = -(-n_time // world)
+    return [(min(r * per, n_time), max(0, min(per, n_time - r * per))) for r in range(world)]
+
+
+def combine_scatter(time_part, r_int_part: float, group=None):
+    """Reduce-scatter a shard's time response over t: every rank sends its
+    part of the whole [n_time, plane] sum and keeps the sum of its own block of
+    time rows (time_row_blocks), half the traffic of an all-reduce.  Returns
+    (rows, first_row, R_int): rows is this rank's block [count, plane] of the
+    pulse's time response (complex128, on time_part's device) and R_int the
+    pulse's.  A process group of one rank (or none) returns time_part whole."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size(group) == 1:
+        return time_part, 0, float(r_int_part)
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    n_time, plane = time_part.shape
+    per = -(-n_time // world)
+    flat = torch.view_as_real(time_part).reshape(-1)
+    if per * world != n_time:
+        pad = torch.zeros((per * world - n_time) * plane * 2, dtype=flat.dtype, device=flat.device)
+        flat = torch.cat([flat, pad])
+    out = torch.empty(per * plane * 2, dtype=flat.dtype, device=flat.device)
+    dist.reduce_scatter_tensor(out, flat, op=dist.ReduceOp.SUM, group=group)
+    first, cnt = time_row_blocks(n_time, world)[rank]
+    rows = torch.view_as_complex(out.view(per, plane, 2))[:cnt]
+    r = torch.tensor([float(r_int_part)], dtype=torch.float64, device=time_part.device)
+    dist.all_reduce(r, op=dist.ReduceOp.SUM, group=group)
+    return rows, first, float(r.item())
 
 
 def shard_plan(w, rank: int, world: int, stream=None):

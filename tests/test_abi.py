@@ -58,3 +58,29 @@ def test_tune_file_parsing_without_a_gpu(tmp_path):
         bpm.tune_load(str(bad))
     with pytest.raises(bpm.BpmError):
         bpm.tune_load(str(tmp_path / "missing.txt"))
+
+
+def test_noalloc_binding_refuses_bad_buffers_before_any_library_call(monkeypatch):
+    """bpm_run_noalloc takes no buffer sizes, so the binding checks every tensor
+    (CUDA, dtype, contiguity, element count) and raises before it loads or calls
+    the library.  Without a GPU every tensor here is refused; the GPU suite
+    (tests/test_zz_no_alloc.py) refuses mis-sized CUDA tensors the same way."""
+    import torch
+    from paper_2201_08500_gb300 import workloads
+
+    def no_library(*a, **k):
+        raise AssertionError("the library was reached")
+
+    monkeypatch.setattr(bpm, "load", no_library)
+    w = workloads.tiny(n_ch=4)
+    good = torch.zeros((w.n_ch, w.nx), dtype=torch.complex64)
+    R = torch.zeros(w.n_ch, dtype=torch.float64)
+    for e0, eh, r in [(good, good, R),                                  # host tensors
+                      (good[:, :-1], good, R),                          # too few elements
+                      (good.to(torch.complex128), good, R),             # wrong dtype
+                      (good, good.t(), R),                              # not contiguous
+                      (good, good, R[:-1]),
+                      (good.numpy(), good, R)]:                         # not a tensor
+        with pytest.raises(bpm.BpmError) as ei:
+            bpm.run_noalloc(w, e0, eh, r)
+        assert ei.value.status == 1 and "run_noalloc" in str(ei.value)

@@ -184,6 +184,8 @@ def test_deformed_full_size_sampled_channels(stream):
     pick = [0, 340, 512, 1023]
     e = errors(w, g, channels=pick)
     assert e["per_ch"] < TOL_FIELD, e
+    # each field over the sampled channels, relative to its own norm
+    assert e["rel0"] < TOL_FIELD and e["relh"] < TOL_FIELD, e
     R = g["refl"][0]
     assert np.max(np.abs(R[pick] - e["oR"])) < 1e-5
     assert np.all(np.isfinite(g["e0"])) and np.all(np.isfinite(g["eh"]))

@@ -588,14 +588,17 @@ def test_strain_gradient_interbranch_fraction():
     beta/beta_c = 4.7326, no absorption.  The fraction of the incident power
     carried by the newly created branch is exp(-2 pi beta_c/|beta|) = 0.2651
     (the paper reports agreement to better than 0.1 %); the rest is reflected.
-    Measured here at 1e-3 relative (tolerance 1.5e-3); the flux leaving the
-    crystal balances the incident flux to the Zassenhaus factor's 1e-3 loss."""
+    Held to the paper's own 0.1 %: the oracle gives 9.9e-4 relative, and that
+    residual is not discretisation (9.5e-4 at dz/2, 9.1e-4 at dz/4, 9.9e-4 at
+    dx/2), i.e. it is the scheme's distance from the asymptotic Landau-Zener
+    formula.  The flux leaving the crystal balances the incident flux to the
+    Zassenhaus factor's 1e-3 loss."""
     w = workloads.strain_gradient()
     e0, eh, init = orc.run(w, n_threads=1)
     trans, refl = _branch_fractions(w, e0, eh, init)
     lz = w.meta["interbranch"]
     assert abs(lz - 0.2651023751753087) < 1e-12
-    assert abs(trans / lz - 1.0) < 1.5e-3, trans
+    assert abs(trans / lz - 1.0) < 1.0e-3, trans
     assert abs(trans + refl - 1.0) < 1e-3, (trans, refl)
 
 

@@ -1,6 +1,7 @@
 """Frequency sharding of one pulse across ranks, host side on CPU: three gloo
 ranks (127.0.0.1) each hold a channel block's part of the time response, and
-one sum-reduce gives the whole pulse's (Section 3.3: the channels are
+one sum-reduce (an all-reduce, or a reduce-scatter over t) gives the whole
+pulse's (Section 3.3: the channels are
 independent; the time response and R_int are the only sums over them)."""
 import os
 import socket
@@ -56,8 +57,10 @@ def _rank(rank, world, port, n, plane, domega, out):
     part[first:first + cnt] = eh[first:first + cnt]       # the other ranks' channels count as zero
     t = torch.from_numpy(orc.omega_to_t(part.astype(np.complex128), domega))
     R = np.linspace(0.1, 0.9, n)                          # stand-in per-channel reflectivities
+    t2 = torch.from_numpy(orc.omega_to_t(part.astype(np.complex128), domega))
+    rows, row0, r_int2 = sh.combine_scatter(t2, domega * float(R[first:first + cnt].sum()))
     r_int = sh.combine(t, domega * float(R[first:first + cnt].sum()))
-    out[rank] = (t.numpy(), r_int)
+    out[rank] = (t.numpy(), r_int, rows.numpy().copy(), row0, r_int2)
     dist.barrier()
     dist.destroy_process_group()
 
@@ -80,9 +83,15 @@ def test_three_gloo_ranks_sum_their_parts_to_the_whole_time_response():
         res = dict(out)
     full = orc.omega_to_t(_spectrum(n, plane).astype(np.complex128), domega)
     for r in range(3):
-        t, r_int = res[r]
+        t, r_int, _, _, r_int2 = res[r]
         assert np.max(np.abs(t - full)) <= 1e-12 * np.max(np.abs(full))
         assert r_int == pytest.approx(domega * np.linspace(0.1, 0.9, n).sum(), rel=1e-14)
+        assert r_int2 == pytest.approx(r_int, rel=1e-14)
+    # reduce-scatter over t: blocks of ceil(8 / 3) = 3 rows, the last one shorter
+    assert [(res[r][3], res[r][2].shape[0]) for r in range(3)] == shard.time_row_blocks(n, 3) \
+        == [(0, 3), (3, 3), (6, 2)]
+    got = np.concatenate([res[r][2] for r in range(3)])
+    assert np.max(np.abs(got - full)) <= 1e-12 * np.max(np.abs(full))
 
 
 def test_a_shard_part_carries_the_global_channel_phase():

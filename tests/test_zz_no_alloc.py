@@ -1,13 +1,16 @@
 """The allocation-free entry point, bpm_run_noalloc, against the plan-based path.
 
 bpm_run_noalloc is for callers that must not allocate device memory while they
-run this code (work recorded into a CUDA graph, memory owned by a caller-side
-pool, latency-bound loops).  Its intermediate buffers live in one fixed device
-array shared by all calls, so this test makes two different calls in a row and
-checks each against bpm_plan_create + bpm_run on the same inputs, within the
-parity tolerance of the other GPU tests.  It also checks that a request beyond
-the array's limits is refused with a clear error.  The file is named so that
-pytest collects it last; it passes alone in a fresh process as well.
+run this code (a process whose device memory a caller-side pool owns, or a
+latency-bound loop that must not take the allocator's lock).  Its intermediate
+buffers live in one fixed device array shared by all calls, so this test makes
+two different calls in a row and checks each against bpm_plan_create + bpm_run
+on the same inputs.  Both run the same setup and march kernels on the same
+inputs, so the results must be bitwise equal (which also holds them within the
+parity tolerance of the other GPU tests).  It also checks that a request beyond
+the array's limits, and a caller buffer of the wrong size, are refused with a
+clear error.  The file is named so that pytest collects it last; it passes
+alone in a fresh process as well.
 """
 import numpy as np
 import pytest
@@ -64,9 +67,11 @@ def test_noalloc_matches_plan_path_on_two_calls_in_a_row():
         outs.append((e0, eh, R, u))
     torch.cuda.synchronize()
     for (e0, eh, R, _), (r0, rh, rR) in zip(outs, refs):
-        assert rel(e0.cpu().numpy(), r0) < TOL_FIELD
-        assert rel(eh.cpu().numpy(), rh) < TOL_FIELD
-        assert np.max(np.abs(R.cpu().numpy() - rR)) < TOL_R
+        g0, gh, gR = e0.cpu().numpy(), eh.cpu().numpy(), R.cpu().numpy()
+        assert rel(g0, r0) < TOL_FIELD and rel(gh, rh) < TOL_FIELD
+        assert np.max(np.abs(gR - rR)) < TOL_R
+        # same kernels, same inputs: bitwise equal
+        assert np.array_equal(g0, r0) and np.array_equal(gh, rh) and np.array_equal(gR, rR)
         assert np.linalg.norm(rh) > 1e-3 * np.linalg.norm(r0)
 
 
@@ -79,3 +84,18 @@ def test_noalloc_refuses_sizes_beyond_its_array():
         bpm.run_noalloc(w, e0, torch.empty_like(e0),
                         torch.empty(w.n_ch, dtype=torch.float64, device="cuda"))
     assert ei.value.status == 4 and "n_channels" in str(ei.value)
+
+
+def test_noalloc_refuses_a_mis_sized_output_buffer():
+    import torch
+    torch.cuda.set_device(0)
+    w = small_case(1024, 100, 4, seed=4)
+    e0 = torch.empty((w.n_ch, w.nx), dtype=torch.complex64, device="cuda")
+    short = torch.empty((w.n_ch, w.nx - 1), dtype=torch.complex64, device="cuda")
+    R = torch.empty(w.n_ch, dtype=torch.float64, device="cuda")
+    with pytest.raises(bpm.BpmError) as ei:
+        bpm.run_noalloc(w, e0, short, R)
+    assert ei.value.status == 1 and "eh_out" in str(ei.value)
+    with pytest.raises(bpm.BpmError):
+        bpm.run_noalloc(w, e0, e0, R, u_dev=torch.zeros(w.nz * w.nx - 1, dtype=torch.float64,
+                                                          device="cuda"))

@@ -27,8 +27,25 @@ namespace bpm {
 
 #define BPM_DEV __device__ __forceinline__
 
+// Complex sums in packed FP32: one Blackwell two-lane instruction (FADD2 /
+// FFMA2, sm_100 and later) does both components, each rounded exactly like the
+// scalar operation, so the butterflies' additions take half the issue slots.
+// a - b is fma(b, -1, a): b * -1 is exact, so the one rounding is that of a - b.
+#ifndef BPM_PACKED_F32
+#define BPM_PACKED_F32 1
+#endif
+#if BPM_PACKED_F32
+BPM_DEV float2 c_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+BPM_DEV float2 c_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+// p * s + a per component (one rounding each)
+BPM_DEV float2 c_fmas(float2 p, float s, float2 a) { return __ffma2_rn(p, make_float2(s, s), a); }
+#else
 BPM_DEV float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 BPM_DEV float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+BPM_DEV float2 c_fmas(float2 p, float s, float2 a) {
+  return make_float2(fmaf(p.x, s, a.x), fmaf(p.y, s, a.y));
+}
+#endif
 BPM_DEV float2 c_mul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -95,19 +112,41 @@ struct Pad {
   }
 };
 
+BPM_DEV float2 c_swap(float2 z) { return make_float2(z.y, z.x); }
+
+// b = d0 -+ i s d1 and d = d0 +- i s d1 (forward: -i, INV: +i): the outputs of
+// a 4-point butterfly that take d1 turned by a quarter turn (and scaled by s).
+// PJ: as two packed FMAs of the swapped pair (d1.y, d1.x), which costs a
+// register swap; otherwise four scalar FMAs.  The rounding is the same either
+// way (one rounding per component), so PJ only trades issue slots against
+// registers: it measured faster in the parked 2048- and 4096-point marches and
+// slower at 8192 points and in the 3D passes, which hold more live values.
+template <bool INV, bool PJ>
+BPM_DEV void jout(float2 d0, float2 d1, float s, float2& b, float2& d) {
+#if BPM_PACKED_F32
+  if constexpr (PJ) {
+    const float2 q = c_swap(d1);
+    b = __ffma2_rn(q, INV ? make_float2(-s, s) : make_float2(s, -s), d0);
+    d = __ffma2_rn(q, INV ? make_float2(s, -s) : make_float2(-s, s), d0);
+    return;
+  }
+#endif
+  if (!INV) {
+    b = make_float2(fmaf(d1.y, s, d0.x), fmaf(-d1.x, s, d0.y));
+    d = make_float2(fmaf(-d1.y, s, d0.x), fmaf(d1.x, s, d0.y));
+  } else {
+    b = make_float2(fmaf(-d1.y, s, d0.x), fmaf(d1.x, s, d0.y));
+    d = make_float2(fmaf(d1.y, s, d0.x), fmaf(-d1.x, s, d0.y));
+  }
+}
+
 // 4-point DFT in place: forward y_m = sum_k v_k exp(-2 pi i k m / 4); INV conjugates.
-template <bool INV>
+template <bool INV, bool PJ = false>
 BPM_DEV void dft4(float2& a, float2& b, float2& c, float2& d) {
   const float2 s0 = c_add(a, c), d0 = c_sub(a, c), s1 = c_add(b, d), d1 = c_sub(b, d);
   a = c_add(s0, s1);
   c = c_sub(s0, s1);
-  if (!INV) {
-    b = make_float2(d0.x + d1.y, d0.y - d1.x);
-    d = make_float2(d0.x - d1.y, d0.y + d1.x);
-  } else {
-    b = make_float2(d0.x - d1.y, d0.y + d1.x);
-    d = make_float2(d0.x + d1.y, d0.y - d1.x);
-  }
+  jout<INV, PJ>(d0, d1, 1.f, b, d);
 }
 
 BPM_DEV void dft2(float2& a, float2& b) {
@@ -160,44 +199,32 @@ BPM_DEV float2 pre8(float2 z) {
 }
 
 // Outputs of a 4-point DFT from s0 = a + c, d0 = a - c, s1 = b + d, d1 = b - d.
-template <bool INV>
+template <bool INV, bool PJ>
 BPM_DEV void dft4_out(float2 s0, float2 d0, float2 s1, float2 d1, float2& a, float2& b, float2& c,
                       float2& d) {
   a = c_add(s0, s1);
   c = c_sub(s0, s1);
-  if (!INV) {
-    b = make_float2(d0.x + d1.y, d0.y - d1.x);
-    d = make_float2(d0.x - d1.y, d0.y + d1.x);
-  } else {
-    b = make_float2(d0.x - d1.y, d0.y + d1.x);
-    d = make_float2(d0.x + d1.y, d0.y - d1.x);
-  }
+  jout<INV, PJ>(d0, d1, 1.f, b, d);
 }
 
 // dft4 whose input c still owes the rotation W16^E (E = 2 or 6).
-template <int E, bool INV>
+template <int E, bool INV, bool PJ>
 BPM_DEV void dft4_c(float2& a, float2& b, float2& c, float2& d) {
   const float2 p = pre8<E, INV>(c);
-  const float2 s0 = make_float2(fmaf(p.x, BPM_C8, a.x), fmaf(p.y, BPM_C8, a.y));
-  const float2 d0 = make_float2(fmaf(-p.x, BPM_C8, a.x), fmaf(-p.y, BPM_C8, a.y));
-  dft4_out<INV>(s0, d0, c_add(b, d), c_sub(b, d), a, b, c, d);
+  const float2 s0 = c_fmas(p, BPM_C8, a);
+  const float2 d0 = c_fmas(p, -BPM_C8, a);
+  dft4_out<INV, PJ>(s0, d0, c_add(b, d), c_sub(b, d), a, b, c, d);
 }
 
 // dft4 whose input b still owes W16^2 and d still owes W16^6.
-template <bool INV>
+template <bool INV, bool PJ>
 BPM_DEV void dft4_bd(float2& a, float2& b, float2& c, float2& d) {
   const float2 pb = pre8<2, INV>(b), pd = pre8<6, INV>(d);
   const float2 P = c_add(pb, pd), Q = c_sub(pb, pd);  // s1 = c8 P, d1 = c8 Q
   const float2 s0 = c_add(a, c), d0 = c_sub(a, c);
-  a = make_float2(fmaf(P.x, BPM_C8, s0.x), fmaf(P.y, BPM_C8, s0.y));
-  c = make_float2(fmaf(-P.x, BPM_C8, s0.x), fmaf(-P.y, BPM_C8, s0.y));
-  if (!INV) {
-    b = make_float2(fmaf(Q.y, BPM_C8, d0.x), fmaf(-Q.x, BPM_C8, d0.y));
-    d = make_float2(fmaf(-Q.y, BPM_C8, d0.x), fmaf(Q.x, BPM_C8, d0.y));
-  } else {
-    b = make_float2(fmaf(-Q.y, BPM_C8, d0.x), fmaf(Q.x, BPM_C8, d0.y));
-    d = make_float2(fmaf(Q.y, BPM_C8, d0.x), fmaf(-Q.x, BPM_C8, d0.y));
-  }
+  a = c_fmas(P, BPM_C8, s0);
+  c = c_fmas(P, -BPM_C8, s0);
+  jout<INV, PJ>(d0, Q, BPM_C8, b, d);
 }
 
 // 16-point DFT of v[0..15] as 4 x 4: k = 4 k1 + k2, m = m1 + 4 m2.
@@ -206,10 +233,10 @@ BPM_DEV void dft4_bd(float2& a, float2& b, float2& c, float2& d) {
 // twiddles inside the second butterflies (fewer instructions; the march
 // kernels); otherwise each twiddle is rounded on its own (the 3D passes, where
 // the fused form cost registers and measured slower).
-template <bool FUSE = true>
+template <bool FUSE = true, bool PJ = FUSE>
 BPM_DEV void dft16_fwd(float2 (&v)[16]) {
 #pragma unroll
-  for (int k2 = 0; k2 < 4; ++k2) dft4<false>(v[k2], v[k2 + 4], v[k2 + 8], v[k2 + 12]);
+  for (int k2 = 0; k2 < 4; ++k2) dft4<false, PJ>(v[k2], v[k2 + 4], v[k2 + 8], v[k2 + 12]);
   v[5] = w16<1, false>(v[5]);
   v[7] = w16<3, false>(v[7]);
   v[10] = w16<4, false>(v[10]);
@@ -218,10 +245,10 @@ BPM_DEV void dft16_fwd(float2 (&v)[16]) {
   // register 4 m1 + k2 holds u[k2][m1]
   if constexpr (FUSE) {
     // the twiddles of v6, v9 (W16^2) and v11, v14 (W16^6) inside the butterflies
-    dft4<false>(v[0], v[1], v[2], v[3]);
-    dft4_c<2, false>(v[4], v[5], v[6], v[7]);
-    dft4_bd<false>(v[8], v[9], v[10], v[11]);
-    dft4_c<6, false>(v[12], v[13], v[14], v[15]);
+    dft4<false, PJ>(v[0], v[1], v[2], v[3]);
+    dft4_c<2, false, PJ>(v[4], v[5], v[6], v[7]);
+    dft4_bd<false, PJ>(v[8], v[9], v[10], v[11]);
+    dft4_c<6, false, PJ>(v[12], v[13], v[14], v[15]);
   } else {
     v[6] = w16<2, false>(v[6]);
     v[9] = w16<2, false>(v[9]);
@@ -229,7 +256,7 @@ BPM_DEV void dft16_fwd(float2 (&v)[16]) {
     v[14] = w16<6, false>(v[14]);
 #pragma unroll
     for (int m1 = 0; m1 < 4; ++m1)
-      dft4<false>(v[4 * m1], v[4 * m1 + 1], v[4 * m1 + 2], v[4 * m1 + 3]);
+      dft4<false, PJ>(v[4 * m1], v[4 * m1 + 1], v[4 * m1 + 2], v[4 * m1 + 3]);
   }
   // register 4 m1 + m2 holds y[m1 + 4 m2]: transpose (register renaming only)
   float2 o[16];
@@ -242,7 +269,7 @@ BPM_DEV void dft16_fwd(float2 (&v)[16]) {
 }
 
 // Exact adjoint of dft16_fwd (unnormalised inverse DFT): y[m] in v[m] -> x[k] in v[k].
-template <bool FUSE = true>
+template <bool FUSE = true, bool PJ = FUSE>
 BPM_DEV void dft16_inv(float2 (&v)[16]) {
   float2 o[16];
 #pragma unroll
@@ -250,7 +277,8 @@ BPM_DEV void dft16_inv(float2 (&v)[16]) {
 #pragma unroll
     for (int m2 = 0; m2 < 4; ++m2) o[4 * m1 + m2] = v[m1 + 4 * m2];
 #pragma unroll
-  for (int m1 = 0; m1 < 4; ++m1) dft4<true>(o[4 * m1], o[4 * m1 + 1], o[4 * m1 + 2], o[4 * m1 + 3]);
+  for (int m1 = 0; m1 < 4; ++m1)
+    dft4<true, PJ>(o[4 * m1], o[4 * m1 + 1], o[4 * m1 + 2], o[4 * m1 + 3]);
   o[5] = w16<1, true>(o[5]);
   o[7] = w16<3, true>(o[7]);
   o[10] = w16<4, true>(o[10]);
@@ -258,28 +286,28 @@ BPM_DEV void dft16_inv(float2 (&v)[16]) {
   o[15] = w16<9, true>(o[15]);
   if constexpr (FUSE) {
     // o6, o9 (conj W16^2) and o11, o14 (conj W16^6) rotate inside the butterflies
-    dft4<true>(o[0], o[4], o[8], o[12]);
-    dft4_c<2, true>(o[1], o[5], o[9], o[13]);
-    dft4_bd<true>(o[2], o[6], o[10], o[14]);
-    dft4_c<6, true>(o[3], o[7], o[11], o[15]);
+    dft4<true, PJ>(o[0], o[4], o[8], o[12]);
+    dft4_c<2, true, PJ>(o[1], o[5], o[9], o[13]);
+    dft4_bd<true, PJ>(o[2], o[6], o[10], o[14]);
+    dft4_c<6, true, PJ>(o[3], o[7], o[11], o[15]);
   } else {
     o[6] = w16<2, true>(o[6]);
     o[9] = w16<2, true>(o[9]);
     o[11] = w16<6, true>(o[11]);
     o[14] = w16<6, true>(o[14]);
 #pragma unroll
-    for (int k2 = 0; k2 < 4; ++k2) dft4<true>(o[k2], o[k2 + 4], o[k2 + 8], o[k2 + 12]);
+    for (int k2 = 0; k2 < 4; ++k2) dft4<true, PJ>(o[k2], o[k2 + 4], o[k2 + 8], o[k2 + 12]);
   }
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = o[i];
 }
 
 // 8-point DFT of v[OFF..OFF+7] as 4 x 2: k = 2 k1 + k2, m = m1 + 4 m2.
-template <int OFF>
+template <int OFF, bool PJ>
 BPM_DEV void dft8_fwd(float2 (&v)[16]) {
   float2* w = v + OFF;
-  dft4<false>(w[0], w[2], w[4], w[6]);
-  dft4<false>(w[1], w[3], w[5], w[7]);
+  dft4<false, PJ>(w[0], w[2], w[4], w[6]);
+  dft4<false, PJ>(w[1], w[3], w[5], w[7]);
   // register 2 m1 + k2 holds u[k2][m1]; twiddle W8^(k2 m1) = W16^(2 k2 m1)
   w[3] = w16<2, false>(w[3]);
   w[5] = w16<4, false>(w[5]);
@@ -295,7 +323,7 @@ BPM_DEV void dft8_fwd(float2 (&v)[16]) {
   for (int i = 0; i < 8; ++i) w[i] = o[i];
 }
 
-template <int OFF>
+template <int OFF, bool PJ>
 BPM_DEV void dft8_inv(float2 (&v)[16]) {
   float2* w = v + OFF;
   float2 o[8];
@@ -308,22 +336,28 @@ BPM_DEV void dft8_inv(float2 (&v)[16]) {
   o[3] = w16<2, true>(o[3]);
   o[5] = w16<4, true>(o[5]);
   o[7] = w16<6, true>(o[7]);
-  dft4<true>(o[0], o[2], o[4], o[6]);
-  dft4<true>(o[1], o[3], o[5], o[7]);
+  dft4<true, PJ>(o[0], o[2], o[4], o[6]);
+  dft4<true, PJ>(o[1], o[3], o[5], o[7]);
 #pragma unroll
   for (int i = 0; i < 8; ++i) w[i] = o[i];
 }
 
 // Last-stage butterflies: 16/R independent R-point DFTs on consecutive registers.
-template <int R, bool INV, bool FUSE = true>
+template <int R, bool INV, bool FUSE = true, bool PJ = FUSE>
 BPM_DEV void last_stage(float2 (&v)[16]) {
   if constexpr (R == 16) {
-    if (INV) dft16_inv<FUSE>(v); else dft16_fwd<FUSE>(v);
+    if (INV) dft16_inv<FUSE, PJ>(v); else dft16_fwd<FUSE, PJ>(v);
   } else if constexpr (R == 8) {
-    if (INV) { dft8_inv<0>(v); dft8_inv<8>(v); } else { dft8_fwd<0>(v); dft8_fwd<8>(v); }
+    if (INV) {
+      dft8_inv<0, PJ>(v);
+      dft8_inv<8, PJ>(v);
+    } else {
+      dft8_fwd<0, PJ>(v);
+      dft8_fwd<8, PJ>(v);
+    }
   } else if constexpr (R == 4) {
 #pragma unroll
-    for (int g = 0; g < 4; ++g) dft4<INV>(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+    for (int g = 0; g < 4; ++g) dft4<INV, PJ>(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
   } else {
     static_assert(R == 2, "last-stage radix");
 #pragma unroll

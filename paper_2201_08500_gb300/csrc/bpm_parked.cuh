@@ -62,6 +62,10 @@ struct Parked {
   // 512-thread block) and in the work-queue kernels the narrower per-element
   // layout spills less and measured faster.
   static constexpr bool kWide = WIDE;
+  // Packed quarter-turn butterfly outputs (jout in bpm_fft.cuh): measured
+  // faster at N <= 4096; at 8192, which spills at 128 registers, the scalar
+  // outputs measured faster.
+  static constexpr bool kPJ = (N <= 4096);
 
   __host__ __device__ static constexpr size_t xbuf_bytes() { return size_t(Pad<N>::kSlots) * sizeof(float2); }
   __host__ __device__ static constexpr size_t red_bytes() { return 64 * sizeof(double); }
@@ -95,7 +99,7 @@ struct Parked {
   template <int s>
   static BPM_DEV void stage_fwd(float2 (&v)[16], const float4* tw, int t) {
     if constexpr (s < S - 1) {
-      dft16_fwd(v);
+      dft16_fwd<true, kPJ>(v);
       if constexpr (kWide) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -109,7 +113,7 @@ struct Parked {
         for (int m = 1; m < 16; ++m) v[m] = c_mul(v[m], twiddle<s>(t1, t, m));
       }
     } else {
-      last_stage<Gm::RLAST, false>(v);
+      last_stage<Gm::RLAST, false, true, kPJ>(v);
     }
   }
 
@@ -128,9 +132,9 @@ struct Parked {
 #pragma unroll
         for (int m = 1; m < 16; ++m) v[m] = c_mulc(v[m], twiddle<s>(t1, t, m));
       }
-      dft16_inv(v);
+      dft16_inv<true, kPJ>(v);
     } else {
-      last_stage<Gm::RLAST, true>(v);
+      last_stage<Gm::RLAST, true, true, kPJ>(v);
     }
   }
 

@@ -53,28 +53,30 @@ FP32_LANES_PER_SM = 128
 TOL_FIELD = 1e-4
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
-# default march, from one ncu capture of that launch per launch form: form 0
-# 597.55 MB read + 62.88 MB written, form 3 535.22 + 54.93 MB.  The deformation
-# rows are re-read by each wave of channels, which at ~9 GB/s is immaterial to
-# this ALU-bound kernel.  Keyed by kernel, form and workload; any other
-# configuration reports null.
+# default march, from one ncu capture of that launch (form 3 with the packed
+# FP32 butterflies: 555.43 MB read + 55.04 MB written).  The deformation rows
+# are re-read by each wave of channels, which at ~10 GB/s is immaterial to this
+# ALU-bound kernel.  Keyed by kernel, form and workload; any other
+# configuration (or a kernel changed since the capture) reports null.
 MEASURED_TRAFFIC = {
-    ("march_kernel<4096,1> form 0", "deformed-2d-nx4096-nz2000-ch1024", 1): 660.43e6,
-    ("march_kernel<4096,1> form 3", "deformed-2d-nx4096-nz2000-ch1024", 1): 590.15e6,
+    ("march_kernel<4096,1> form 3", "deformed-2d-nx4096-nz2000-ch1024", 1): 610.46e6,
 }
 # Executed FP32 flop per cell-update (FADD + FMUL + 2 FFMA thread instructions,
 # ncu, per kernel and form): the work the kernel really issues, against the
-# nominal count of flops_per_cell.
+# nominal count of flops_per_cell.  Counted on the build with scalar
+# butterfly additions; the packed build performs the same operations (its
+# fields are bitwise equal at these sizes), and ncu's per-opcode FP32 counters
+# do not resolve the packed two-lane instructions.
 EXECUTED_FLOPS = {
     "march_kernel<4096,1> form 3": 210.0,
     "march_kernel<8192,1> form 3": 240.0,
 }
-# DRAM bytes of one z step of the 3D workload (one column pass + one MODE-1 row
-# pass, 256-thread row tile), from the live launch list of those launches with
-# --cache-control none: 1239 + 1085 MB.  Algorithmic: 64 B per cell-update =
-# 2147 MB; the excess is the row pass's output draining from L2 during the
-# column pass.
-MEASURED_TRAFFIC_3D = {("large-3d-512x512-nz1000-ch128", 0, 256): 2323.87e6}
+# DRAM bytes of one z step of the 3D workload (one streamed column pass, launch
+# form 1, + one MODE-1 row pass, 256-thread row tile), from the live launch
+# list of those launches with --cache-control none: 1065.5 + 1086.3 MB, the
+# algorithmic 64 B per cell-update (2147 MB) within 0.2 %.
+MEASURED_TRAFFIC_3D = {("large-3d-512x512-nz1000-ch128", 1, 256): (539.5e6 + 526.0e6 + 539.8e6
+                                                                     + 546.5e6)}
 
 
 def flops_per_cell(n: int, split_order: int = 1) -> float:

@@ -33,6 +33,7 @@
 
 #include "bpm_fft.cuh"
 #include "bpm_internal.h"
+#include "bpm_tma.cuh"
 
 namespace bpm {
 namespace {
@@ -362,6 +363,186 @@ __global__ void __launch_bounds__(kColThreads, 2) col_pass_kernel(Pass3DArgs A) 
   }
 }
 
+// Single-envelope transform of N points held by a group of T = N/16 threads,
+// exchanging through the group's own region of Pad<N>::kSlots 64-bit slots
+// (the padded layout of the 1D march: conflict-free, one base register per
+// pattern).  Butterflies, twiddles and their order are those of Fft2Env, so
+// every element is computed bitwise as there.
+template <int N>
+struct Fft1Env {
+  using Gm = Geom<N>;
+  static constexpr int T = Gm::T;
+  static constexpr int S = Gm::S;
+
+  template <int s>
+  static BPM_DEV void twid(float2 (&a)[16], const float2* tw, int t, bool inv) {
+    constexpr int ln = Gm::LN(s);
+    const float2* ts = tw + Fft2Env<N>::tw_off(s) + (t % ln);
+#pragma unroll
+    for (int m = 1; m < 16; ++m) {
+      const float2 w = __ldg(ts + (m - 1) * ln);
+      a[m] = inv ? c_mulc(a[m], w) : c_mul(a[m], w);
+    }
+  }
+
+  template <int SF, int ST>
+  static BPM_DEV void xchg(float2 (&a)[16], float2* buf, int t, int g) {
+    g3_sync<T>(g);  // the group's loads of the previous exchange are done
+    float2* st = buf + Pad<N>::template base<SF>(t);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) st[Pad<N>::template off<SF>(k)] = a[k];
+    g3_sync<T>(g);
+    const float2* ld = buf + Pad<N>::template base<ST>(t);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) a[k] = ld[Pad<N>::template off<ST>(k)];
+  }
+
+  template <int s>
+  static BPM_DEV void sfwd(float2 (&a)[16], const float2* tw, int t) {
+    if constexpr (s < S - 1) {
+      dft16_fwd<false>(a);
+      twid<s>(a, tw, t, false);
+    } else {
+      last_stage<Gm::RLAST, false, false>(a);
+    }
+  }
+
+  template <int s>
+  static BPM_DEV void sinv(float2 (&a)[16], const float2* tw, int t) {
+    if constexpr (s < S - 1) {
+      twid<s>(a, tw, t, true);
+      dft16_inv<false>(a);
+    } else {
+      last_stage<Gm::RLAST, true, false>(a);
+    }
+  }
+
+  static BPM_DEV void fwd(float2 (&a)[16], float2* buf, const float2* tw, int t, int g) {
+    static_assert(S == 2 || S == 3, "3D transforms of 256..1024 points");
+    sfwd<0>(a, tw, t);
+    xchg<0, 1>(a, buf, t, g);
+    sfwd<1>(a, tw, t);
+    if constexpr (S == 3) {
+      xchg<1, 2>(a, buf, t, g);
+      sfwd<2>(a, tw, t);
+    }
+  }
+
+  static BPM_DEV void inv(float2 (&a)[16], float2* buf, const float2* tw, int t, int g) {
+    if constexpr (S == 3) {
+      sinv<2>(a, tw, t);
+      xchg<2, 1>(a, buf, t, g);
+    }
+    sinv<1>(a, tw, t);
+    xchg<1, 0>(a, buf, t, g);
+    sinv<0>(a, tw, t);
+  }
+};
+
+// True in every thread of transform group g (T threads) iff `ok` is true in all
+// of them (flags: one int per warp of the block, for T > 32).
+template <int T>
+BPM_DEV bool group_all(bool ok, int g, int* flags) {
+  if constexpr (T == 16) {
+    return __all_sync((threadIdx.x & 16u) ? 0xFFFF0000u : 0x0000FFFFu, ok);
+  } else if constexpr (T == 32) {
+    return __all_sync(0xFFFFFFFFu, ok);
+  } else {
+    const bool w = __all_sync(0xFFFFFFFFu, ok);
+    if ((threadIdx.x & 31) == 0) flags[threadIdx.x / 32] = w ? 1 : 0;
+    g3_sync<T>(g);
+    bool all = true;
+#pragma unroll
+    for (int i = 0; i < T / 32; ++i) all = all && flags[g * (T / 32) + i] != 0;
+    g3_sync<T>(g);
+    return all;
+  }
+}
+
+// Column pass streamed by the copy engine (launch form 1 of 3D plans).
+// Persistent: every group of T = NY/16 threads walks its share of the
+// 2 n_ch nx single-envelope columns (E0 columns first, then Eh; each NY
+// contiguous complex64 in the transposed layout).  While it transforms one
+// column, a bulk copy (cp.async.bulk, completing on the group's mbarrier)
+// brings its next column into the group's stage buffer, so every SM keeps
+// kColTmaBlocksPerSm x 256 / T columns of loads in flight under the
+// arithmetic.  Results are stored straight from registers (coalesced).  The
+// arithmetic of every element is that of col_pass_kernel.
+// A wait that gives up writes kStatusTmaTimeout to *status, waits once more
+// (bounded) for the group's copy in flight and ends the group's work.
+constexpr int kColTmaThreads = 256;
+#ifndef BPM_COL_TMA_BPS
+#define BPM_COL_TMA_BPS 2
+#endif
+constexpr int kColTmaBlocksPerSm = BPM_COL_TMA_BPS;
+
+template <int NY>
+__global__ void __launch_bounds__(kColTmaThreads, kColTmaBlocksPerSm)
+    col_pass_tma_kernel(Pass3DArgs A, int n_ch, int* status) {
+  constexpr int T = NY / 16;
+  constexpr int G = kColTmaThreads / T;  // groups (columns in flight) per block
+  constexpr uint32_t kBytes = NY * sizeof(float2);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int g = threadIdx.x / T;
+  const int t = threadIdx.x % T;
+  float2* stage = reinterpret_cast<float2*>(smem_raw) + size_t(g) * NY;
+  float2* xbuf = reinterpret_cast<float2*>(smem_raw) + size_t(G) * NY + size_t(g) * Pad<NY>::kSlots;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + size_t(G) * (NY + Pad<NY>::kSlots) *
+                                                             sizeof(float2)) + g;
+  int* flags = reinterpret_cast<int*>(bar - g + G);
+  const long long n_cols = (long long)n_ch * A.nx;
+  const long long n_items = 2 * n_cols;
+  const long long stride = (long long)gridDim.x * G;
+  long long item = (long long)blockIdx.x * G + g;
+  if (t == 0) {
+    mbar_init(bar, 1);
+    mbar_init_fence();
+  }
+  g3_sync<T>(g);
+  if (t == 0 && item < n_items) {
+    mbar_arrive_expect_tx(bar, kBytes);
+    bulk_load(stage, (item < n_cols ? A.s0 : A.sh) + (item % n_cols) * NY, kBytes, bar);
+  }
+  uint32_t phase = 0;
+  for (; item < n_items; item += stride) {
+    if (!group_all<T>(mbar_wait(bar, phase), g, flags)) {
+      if (t == 0) atomicExch(status, kStatusTmaTimeout);
+      mbar_wait(bar, phase);  // the copy still in flight, bounded
+      return;
+    }
+    phase ^= 1u;
+    float2 a[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) a[k] = stage[t + T * k];
+    g3_sync<T>(g);  // every read of the stage is done before it is refilled
+    const long long next = item + stride;
+    if (t == 0 && next < n_items) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(bar, kBytes);
+      bulk_load(stage, (next < n_cols ? A.s0 : A.sh) + (next % n_cols) * NY, kBytes, bar);
+    }
+    const int env = item < n_cols ? 0 : 1;
+    const long long cidx = item % n_cols;
+    const int ch = int(cidx / A.nx);
+    const int cs = int(cidx % A.nx);
+    Fft1Env<NY>::fwd(a, xbuf, A.twy, t, g);
+    const float4 an = __ldg(A.anchor + (size_t(ch) * 2 + env) * A.nx + cs);
+    const float gc = __ldg(A.gcorr + (size_t(ch) * 2 + env) * A.nx + cs);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const float2 qd = __ldg(A.qy + k * T + t);  // {qy^2, 1/g_y - 1} at position 16 t + k
+      const float cr = qd.x * gc;
+      const float2 v = c_mul2(a[k], an);
+      const float2 f = make_float2(fmaf(-0.5f * cr, cr, qd.y), cr);
+      a[k] = make_float2(fmaf(v.x, f.x, fmaf(-v.y, f.y, v.x)), fmaf(v.x, f.y, fmaf(v.y, f.x, v.y)));
+    }
+    Fft1Env<NY>::inv(a, xbuf, A.twy, t, g);
+    float2* col = (env == 0 ? A.s0 : A.sh) + cidx * NY;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) col[t + T * k] = a[k];
+  }
+}
+
 // Per-channel sums of |E0|^2 and |Eh|^2 over the plane (FP64), divided by the
 // incident norm.
 __global__ void reduce3d_kernel(const float2* e0, const float2* eh, long long plane,
@@ -407,6 +588,14 @@ size_t col_smem() {
   return size_t(kColThreads / (NY / 16)) * 2 * NY * sizeof(float2);
 }
 
+// Stage buffers, exchange regions, mbarriers and vote flags of col_pass_tma_kernel.
+template <int NY>
+size_t col_tma_smem() {
+  constexpr int G = kColTmaThreads / (NY / 16);
+  return size_t(G) * (NY + Pad<NY>::kSlots) * sizeof(float2) + G * sizeof(uint64_t) +
+         (kColTmaThreads / 32) * sizeof(int);
+}
+
 template <int NX, int MODE, int RT>
 cudaError_t row_launch(const Pass3DArgs& a, int n_ch, cudaStream_t s) {
   constexpr int R = RT / (NX / 16);
@@ -420,6 +609,17 @@ cudaError_t col_launch(const Pass3DArgs& a, int n_ch, cudaStream_t s) {
   constexpr int W = kColThreads / (NY / 16);
   dim3 grid(unsigned(a.nx / W), unsigned(n_ch));
   col_pass_kernel<NY><<<grid, kColThreads, col_smem<NY>(), s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int NY>
+cudaError_t col_tma_launch(const Pass3DArgs& a, int n_ch, int sms, int* status, cudaStream_t s) {
+  constexpr int G = kColTmaThreads / (NY / 16);
+  const long long items = 2LL * n_ch * a.nx;
+  const long long need = (items + G - 1) / G;
+  const int blocks = int(need < (long long)sms * kColTmaBlocksPerSm ? need
+                                                                    : (long long)sms * kColTmaBlocksPerSm);
+  col_pass_tma_kernel<NY><<<blocks, kColTmaThreads, col_tma_smem<NY>(), s>>>(a, n_ch, status);
   return cudaGetLastError();
 }
 
@@ -441,8 +641,12 @@ cudaError_t row_attrs() {
 
 template <int NY>
 cudaError_t col_attrs() {
-  return cudaFuncSetAttribute(col_pass_kernel<NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(col_smem<NY>()));
+  cudaError_t e = cudaFuncSetAttribute(col_pass_kernel<NY>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(col_smem<NY>()));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(col_pass_tma_kernel<NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(col_tma_smem<NY>()));
 }
 
 }  // namespace
@@ -480,7 +684,14 @@ cudaError_t launch_row_pass(int mode, int row_threads, const Pass3DArgs& a, int 
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_col_pass(const Pass3DArgs& a, int n_ch, cudaStream_t s) {
+cudaError_t launch_col_pass(int form, const Pass3DArgs& a, int n_ch, int sms, int* status,
+                            cudaStream_t s) {
+  if (form == 1) {
+    if (a.ny == 256) return col_tma_launch<256>(a, n_ch, sms, status, s);
+    if (a.ny == 512) return col_tma_launch<512>(a, n_ch, sms, status, s);
+    if (a.ny == 1024) return col_tma_launch<1024>(a, n_ch, sms, status, s);
+    return cudaErrorInvalidValue;
+  }
   if (a.ny == 256) return col_launch<256>(a, n_ch, s);
   if (a.ny == 512) return col_launch<512>(a, n_ch, s);
   if (a.ny == 1024) return col_launch<1024>(a, n_ch, s);

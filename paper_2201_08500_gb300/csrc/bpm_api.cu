@@ -334,7 +334,8 @@ TuneKey tune_key(const bpm_grid& g, int n_ch) {
 
 // Whether a plan of grid g can run launch form (form, group, row_threads).
 bool launch_valid(const bpm_grid& g, int form, int group, int row_threads) {
-  if (g.dims == 3) return form == 0 && group == 1 && (row_threads == 256 || row_threads == 512);
+  if (g.dims == 3)
+    return (form == 0 || form == 1) && group == 1 && (row_threads == 256 || row_threads == 512);
   const int maxg = march_max_group(g.nx);
   if (row_threads != 256) return false;
   if (form == 0) return group == 1 || group == maxg;
@@ -787,7 +788,9 @@ BPM_API bpm_status bpm_run(bpm_plan p, int n_steps) {
     march_launches = 1;
     for (int s = 0; s < n_steps; ++s) {
       pa.z = p->z + s;
-      BPM_CUDA(p, launch_col_pass(pa, p->n_ch, p->stream), "column pass");
+      BPM_CUDA(p, launch_col_pass(p->form, pa, p->n_ch, device_info().sm_count, p->dflag + 1,
+                                  p->stream),
+               "column pass");
       BPM_CUDA(p, launch_row_pass(s == n_steps - 1 ? 2 : 1, p->row_threads, pa, p->n_ch, p->stream), "row pass");
       march_launches += 2;
     }
@@ -833,6 +836,15 @@ BPM_API bpm_status bpm_sync(bpm_plan p) {
   BPM_NVTX();
   if (!p) return fail(nullptr, BPM_ERR_INVALID_ARG, "null plan");
   BPM_CUDA(p, cudaStreamSynchronize(p->stream), "stream synchronize");
+  if (p->grid.dims == 3 && p->form == 1) {
+    // status word of the streamed column pass: a bounded wait that gave up
+    int st = 0;
+    BPM_CUDA(p, cudaMemcpy(&st, p->dflag + 1, sizeof(int), cudaMemcpyDeviceToHost), "status");
+    if (st != 0) {
+      BPM_CUDA(p, cudaMemset(p->dflag + 1, 0, sizeof(int)), "clear status");
+      return fail(p, BPM_ERR_TIMEOUT, "3D column pass: a bulk-copy wait gave up");
+    }
+  }
   return BPM_OK;
 }
 
@@ -998,6 +1010,8 @@ BPM_API bpm_status bpm_tune(const bpm_grid* grid, int n_channels, int steps, bpm
     if (g.dims == 3) {
       cand.push_back(bpm_launch{0, 1, 256, 0.f});
       cand.push_back(bpm_launch{0, 1, 512, 0.f});
+      cand.push_back(bpm_launch{1, 1, 256, 0.f});
+      cand.push_back(bpm_launch{1, 1, 512, 0.f});
     } else {
       const int maxg = march_max_group(g.nx);
       cand.push_back(bpm_launch{0, 1, 256, 0.f});

@@ -34,18 +34,31 @@ namespace bpm {
 #ifndef BPM_PACKED_F32
 #define BPM_PACKED_F32 1
 #endif
+// PA selects the packed form; the 3D passes (FUSE = false below) keep the
+// scalar form, which measured faster there (they hold two envelopes and more
+// live values, and the packed pairs cost registers).
+template <bool PA = true>
+BPM_DEV float2 c_add(float2 a, float2 b) {
 #if BPM_PACKED_F32
-BPM_DEV float2 c_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-BPM_DEV float2 c_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+  if constexpr (PA) return __fadd2_rn(a, b);
+#endif
+  return make_float2(a.x + b.x, a.y + b.y);
+}
+template <bool PA = true>
+BPM_DEV float2 c_sub(float2 a, float2 b) {
+#if BPM_PACKED_F32
+  if constexpr (PA) return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+#endif
+  return make_float2(a.x - b.x, a.y - b.y);
+}
 // p * s + a per component (one rounding each)
-BPM_DEV float2 c_fmas(float2 p, float s, float2 a) { return __ffma2_rn(p, make_float2(s, s), a); }
-#else
-BPM_DEV float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-BPM_DEV float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+template <bool PA = true>
 BPM_DEV float2 c_fmas(float2 p, float s, float2 a) {
+#if BPM_PACKED_F32
+  if constexpr (PA) return __ffma2_rn(p, make_float2(s, s), a);
+#endif
   return make_float2(fmaf(p.x, s, a.x), fmaf(p.y, s, a.y));
 }
-#endif
 BPM_DEV float2 c_mul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -141,17 +154,19 @@ BPM_DEV void jout(float2 d0, float2 d1, float s, float2& b, float2& d) {
 }
 
 // 4-point DFT in place: forward y_m = sum_k v_k exp(-2 pi i k m / 4); INV conjugates.
-template <bool INV, bool PJ = false>
+template <bool INV, bool PJ = false, bool PA = true>
 BPM_DEV void dft4(float2& a, float2& b, float2& c, float2& d) {
-  const float2 s0 = c_add(a, c), d0 = c_sub(a, c), s1 = c_add(b, d), d1 = c_sub(b, d);
-  a = c_add(s0, s1);
-  c = c_sub(s0, s1);
+  const float2 s0 = c_add<PA>(a, c), d0 = c_sub<PA>(a, c), s1 = c_add<PA>(b, d),
+               d1 = c_sub<PA>(b, d);
+  a = c_add<PA>(s0, s1);
+  c = c_sub<PA>(s0, s1);
   jout<INV, PJ>(d0, d1, 1.f, b, d);
 }
 
+template <bool PA = true>
 BPM_DEV void dft2(float2& a, float2& b) {
-  const float2 s = c_add(a, b);
-  b = c_sub(a, b);
+  const float2 s = c_add<PA>(a, b);
+  b = c_sub<PA>(a, b);
   a = s;
 }
 
@@ -236,7 +251,7 @@ BPM_DEV void dft4_bd(float2& a, float2& b, float2& c, float2& d) {
 template <bool FUSE = true, bool PJ = FUSE>
 BPM_DEV void dft16_fwd(float2 (&v)[16]) {
 #pragma unroll
-  for (int k2 = 0; k2 < 4; ++k2) dft4<false, PJ>(v[k2], v[k2 + 4], v[k2 + 8], v[k2 + 12]);
+  for (int k2 = 0; k2 < 4; ++k2) dft4<false, PJ, FUSE>(v[k2], v[k2 + 4], v[k2 + 8], v[k2 + 12]);
   v[5] = w16<1, false>(v[5]);
   v[7] = w16<3, false>(v[7]);
   v[10] = w16<4, false>(v[10]);
@@ -256,7 +271,7 @@ BPM_DEV void dft16_fwd(float2 (&v)[16]) {
     v[14] = w16<6, false>(v[14]);
 #pragma unroll
     for (int m1 = 0; m1 < 4; ++m1)
-      dft4<false, PJ>(v[4 * m1], v[4 * m1 + 1], v[4 * m1 + 2], v[4 * m1 + 3]);
+      dft4<false, PJ, FUSE>(v[4 * m1], v[4 * m1 + 1], v[4 * m1 + 2], v[4 * m1 + 3]);
   }
   // register 4 m1 + m2 holds y[m1 + 4 m2]: transpose (register renaming only)
   float2 o[16];
@@ -278,7 +293,7 @@ BPM_DEV void dft16_inv(float2 (&v)[16]) {
     for (int m2 = 0; m2 < 4; ++m2) o[4 * m1 + m2] = v[m1 + 4 * m2];
 #pragma unroll
   for (int m1 = 0; m1 < 4; ++m1)
-    dft4<true, PJ>(o[4 * m1], o[4 * m1 + 1], o[4 * m1 + 2], o[4 * m1 + 3]);
+    dft4<true, PJ, FUSE>(o[4 * m1], o[4 * m1 + 1], o[4 * m1 + 2], o[4 * m1 + 3]);
   o[5] = w16<1, true>(o[5]);
   o[7] = w16<3, true>(o[7]);
   o[10] = w16<4, true>(o[10]);
@@ -296,24 +311,24 @@ BPM_DEV void dft16_inv(float2 (&v)[16]) {
     o[11] = w16<6, true>(o[11]);
     o[14] = w16<6, true>(o[14]);
 #pragma unroll
-    for (int k2 = 0; k2 < 4; ++k2) dft4<true, PJ>(o[k2], o[k2 + 4], o[k2 + 8], o[k2 + 12]);
+    for (int k2 = 0; k2 < 4; ++k2) dft4<true, PJ, FUSE>(o[k2], o[k2 + 4], o[k2 + 8], o[k2 + 12]);
   }
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = o[i];
 }
 
 // 8-point DFT of v[OFF..OFF+7] as 4 x 2: k = 2 k1 + k2, m = m1 + 4 m2.
-template <int OFF, bool PJ>
+template <int OFF, bool PJ, bool PA>
 BPM_DEV void dft8_fwd(float2 (&v)[16]) {
   float2* w = v + OFF;
-  dft4<false, PJ>(w[0], w[2], w[4], w[6]);
-  dft4<false, PJ>(w[1], w[3], w[5], w[7]);
+  dft4<false, PJ, PA>(w[0], w[2], w[4], w[6]);
+  dft4<false, PJ, PA>(w[1], w[3], w[5], w[7]);
   // register 2 m1 + k2 holds u[k2][m1]; twiddle W8^(k2 m1) = W16^(2 k2 m1)
   w[3] = w16<2, false>(w[3]);
   w[5] = w16<4, false>(w[5]);
   w[7] = w16<6, false>(w[7]);
 #pragma unroll
-  for (int m1 = 0; m1 < 4; ++m1) dft2(w[2 * m1], w[2 * m1 + 1]);
+  for (int m1 = 0; m1 < 4; ++m1) dft2<PA>(w[2 * m1], w[2 * m1 + 1]);
   float2 o[8];
 #pragma unroll
   for (int m1 = 0; m1 < 4; ++m1)
@@ -323,7 +338,7 @@ BPM_DEV void dft8_fwd(float2 (&v)[16]) {
   for (int i = 0; i < 8; ++i) w[i] = o[i];
 }
 
-template <int OFF, bool PJ>
+template <int OFF, bool PJ, bool PA>
 BPM_DEV void dft8_inv(float2 (&v)[16]) {
   float2* w = v + OFF;
   float2 o[8];
@@ -332,12 +347,12 @@ BPM_DEV void dft8_inv(float2 (&v)[16]) {
 #pragma unroll
     for (int m2 = 0; m2 < 2; ++m2) o[2 * m1 + m2] = w[m1 + 4 * m2];
 #pragma unroll
-  for (int m1 = 0; m1 < 4; ++m1) dft2(o[2 * m1], o[2 * m1 + 1]);
+  for (int m1 = 0; m1 < 4; ++m1) dft2<PA>(o[2 * m1], o[2 * m1 + 1]);
   o[3] = w16<2, true>(o[3]);
   o[5] = w16<4, true>(o[5]);
   o[7] = w16<6, true>(o[7]);
-  dft4<true, PJ>(o[0], o[2], o[4], o[6]);
-  dft4<true, PJ>(o[1], o[3], o[5], o[7]);
+  dft4<true, PJ, PA>(o[0], o[2], o[4], o[6]);
+  dft4<true, PJ, PA>(o[1], o[3], o[5], o[7]);
 #pragma unroll
   for (int i = 0; i < 8; ++i) w[i] = o[i];
 }
@@ -349,19 +364,20 @@ BPM_DEV void last_stage(float2 (&v)[16]) {
     if (INV) dft16_inv<FUSE, PJ>(v); else dft16_fwd<FUSE, PJ>(v);
   } else if constexpr (R == 8) {
     if (INV) {
-      dft8_inv<0, PJ>(v);
-      dft8_inv<8, PJ>(v);
+      dft8_inv<0, PJ, FUSE>(v);
+      dft8_inv<8, PJ, FUSE>(v);
     } else {
-      dft8_fwd<0, PJ>(v);
-      dft8_fwd<8, PJ>(v);
+      dft8_fwd<0, PJ, FUSE>(v);
+      dft8_fwd<8, PJ, FUSE>(v);
     }
   } else if constexpr (R == 4) {
 #pragma unroll
-    for (int g = 0; g < 4; ++g) dft4<INV, PJ>(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+    for (int g = 0; g < 4; ++g)
+      dft4<INV, PJ, FUSE>(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
   } else {
     static_assert(R == 2, "last-stage radix");
 #pragma unroll
-    for (int g = 0; g < 8; ++g) dft2(v[2 * g], v[2 * g + 1]);
+    for (int g = 0; g < 8; ++g) dft2<FUSE>(v[2 * g], v[2 * g + 1]);
   }
 }
 

@@ -79,6 +79,22 @@ def test_fourth_order_parked_form_gives_identical_fields(nx):
         assert np.array_equal(got[k], ref[k]), k
 
 
+@pytest.mark.parametrize("nx,ny,n_ch", [(512, 256, 3), (256, 512, 5), (256, 1024, 2)])
+def test_3d_streamed_column_pass_gives_identical_fields(nx, ny, n_ch):
+    """Launch form 1 of a 3D plan: the persistent column pass that streams each
+    group's next column in with a bulk copy (mbarrier completion) while it
+    transforms the current one.  Same arithmetic per element as form 0, so the
+    fields are bitwise equal; channel counts leave the last groups short of
+    columns (a ragged end of the persistent walk)."""
+    from test_gpu_3d import case3d
+    w = case3d(nx, ny, 12, n_ch, seed=nx + ny + n_ch)
+    a, used_a = fields(w, form=0, row_threads=256)
+    b, used_b = fields(w, form=1, row_threads=256)
+    assert used_a["form"] == 0 and used_b["form"] == 1
+    for k in ("e0", "eh", "R"):
+        assert np.array_equal(a[k], b[k]), k
+
+
 def test_3d_row_tiles_give_identical_fields():
     from test_gpu_3d import case3d
     w = case3d(512, 256, 16, 2, seed=5)
@@ -126,4 +142,5 @@ def test_tuner_keeps_the_fastest_and_later_plans_use_it(tmp_path):
     q.close()
     b3, every3 = bpm.tune(3, 256, 256, 1e-6, 1e-6, 0.25e-6, 2, steps=4)
     assert {f["row_threads"] for f in every3} == {256, 512}
+    assert {f["form"] for f in every3} == {0, 1}
     bpm.tune_clear()

@@ -80,6 +80,10 @@ const FftConsts& fft_consts(int n) {
     const double a = 2.0 * kPiHost * double(k) / double(n);
     f->tw[k] = make_float2(float(std::cos(a)), float(-std::sin(a)));
   }
+  // the W_32 powers the kernels take as immediates (w32_re / w32_im): the same
+  // correctly rounded values, written here so that kernel and table agree
+  for (int m = 1; m < 16 && n >= 32; ++m)
+    f->tw[size_t(n / 32) * m] = make_float2(w32_re(m), w32_im(m));
   const int logn = ilog2i(n);
   const int S = (logn + 3) / 4;
   const int rlast = n >> (4 * (S - 1));

@@ -22,6 +22,28 @@ struct NvtxRange {
 // march kernel: one radix-16 butterfly group per thread per stage.
 constexpr int kElemsPerThread = 16;
 
+// exp(-2 pi i m / 32) for m = 1..15 in FP32: the correctly rounded cos and
+// -sin of 2 pi m / 32 (m = 8: the FP32 value of cos(pi/2) in double, as the
+// twiddle table holds it).  The 8192-point transform's third radix-16 stage
+// multiplies by W_32^(j m) with j = t % 2, so these are its only twiddles; the
+// kernels take them as immediates instead of loads (the loaded values kept
+// ~30 registers live and made the 512-thread kernels spill), and the host
+// twiddle table uses the same values at k = (n / 32) m.
+__host__ __device__ constexpr float w32_re(int m) {
+  return m == 1 ? 0x1.f6297cp-1f : m == 2 ? 0x1.d906bcp-1f : m == 3 ? 0x1.a9b662p-1f
+       : m == 4 ? 0x1.6a09e6p-1f : m == 5 ? 0x1.1c73b4p-1f : m == 6 ? 0x1.87de2ap-2f
+       : m == 7 ? 0x1.8f8b84p-3f : m == 8 ? 0x1.1a6264p-54f : m == 9 ? -0x1.8f8b84p-3f
+       : m == 10 ? -0x1.87de2ap-2f : m == 11 ? -0x1.1c73b4p-1f : m == 12 ? -0x1.6a09e6p-1f
+       : m == 13 ? -0x1.a9b662p-1f : m == 14 ? -0x1.d906bcp-1f : -0x1.f6297cp-1f;
+}
+__host__ __device__ constexpr float w32_im(int m) {
+  return m == 1 ? -0x1.8f8b84p-3f : m == 2 ? -0x1.87de2ap-2f : m == 3 ? -0x1.1c73b4p-1f
+       : m == 4 ? -0x1.6a09e6p-1f : m == 5 ? -0x1.a9b662p-1f : m == 6 ? -0x1.d906bcp-1f
+       : m == 7 ? -0x1.f6297cp-1f : m == 8 ? -0x1.0p+0f : m == 9 ? -0x1.f6297cp-1f
+       : m == 10 ? -0x1.d906bcp-1f : m == 11 ? -0x1.a9b662p-1f : m == 12 ? -0x1.6a09e6p-1f
+       : m == 13 ? -0x1.1c73b4p-1f : m == 14 ? -0x1.87de2ap-2f : -0x1.8f8b84p-3f;
+}
+
 // Coupling coefficients of Eq. fov10 for one channel, FP32.  a is split into
 // hi + lo parts so that its systematic rounding does not accumulate over the
 // march; b+ (Eh -> E0) and b- (E0 -> Eh) are used once per step and stay FP32.

@@ -107,6 +107,15 @@ struct Parked {
           v[2 * i + 1] = c_mul(v[2 * i + 1], make_float2(w.x, w.y));
           if (i < 7) v[2 * i + 2] = c_mul(v[2 * i + 2], make_float2(w.z, w.w));
         }
+      } else if constexpr (Gm::LN(s) == 2) {
+        // W_32^(j m), j = t % 2: ones on even lanes, the fixed W_32^m on odd
+        // ones, as immediates selected per lane (no loads: the loaded twiddles
+        // made this 512-thread kernel spill 300 B a thread; a branch on the
+        // lane parity instead of the selection measured slower than both)
+        const bool odd = t & 1;
+#pragma unroll
+        for (int m = 1; m < 16; ++m)
+          v[m] = c_mul(v[m], make_float2(odd ? w32_re(m) : 1.f, odd ? w32_im(m) : 0.f));
       } else {
         const float2* t1 = reinterpret_cast<const float2*>(tw);
 #pragma unroll
@@ -127,6 +136,11 @@ struct Parked {
           v[2 * i + 1] = c_mulc(v[2 * i + 1], make_float2(w.x, w.y));
           if (i < 7) v[2 * i + 2] = c_mulc(v[2 * i + 2], make_float2(w.z, w.w));
         }
+      } else if constexpr (Gm::LN(s) == 2) {
+        const bool odd = t & 1;
+#pragma unroll
+        for (int m = 1; m < 16; ++m)
+          v[m] = c_mulc(v[m], make_float2(odd ? w32_re(m) : 1.f, odd ? w32_im(m) : 0.f));
       } else {
         const float2* t1 = reinterpret_cast<const float2*>(tw);
 #pragma unroll

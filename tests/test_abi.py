@@ -84,3 +84,25 @@ def test_noalloc_binding_refuses_bad_buffers_before_any_library_call(monkeypatch
         with pytest.raises(bpm.BpmError) as ei:
             bpm.run_noalloc(w, e0, eh, r)
         assert ei.value.status == 1 and "run_noalloc" in str(ei.value)
+
+
+def test_w32_twiddle_constants_are_the_correctly_rounded_values():
+    """The 8192-point kernels take the W_32 powers of their third stage as
+    immediates (w32_re / w32_im in csrc/bpm_internal.h), and the host twiddle
+    table uses the same values: they must be the FP32 roundings of cos and
+    -sin of 2 pi m / 32 (m = 8: of the double cos(pi/2))."""
+    import numpy as np
+    txt = open(os.path.join(ROOT, "paper_2201_08500_gb300", "csrc", "bpm_internal.h")).read()
+
+    def values(name):
+        body = txt[txt.index(f"constexpr float {name}(int m)"):]
+        body = body[:body.index("}")]
+        lits = re.findall(r"(-?0x[0-9a-f.]+p[-+]?\d+)f", body)
+        assert len(lits) == 15, (name, lits)
+        return [float.fromhex(x) for x in lits]
+
+    re_, im_ = values("w32_re"), values("w32_im")
+    for m in range(1, 16):
+        a = 2.0 * np.pi * float(256 * m) / 8192.0        # the host's angle for k = 256 m, n = 8192
+        assert re_[m - 1] == float(np.float32(np.cos(a))), m
+        assert im_[m - 1] == float(np.float32(-np.sin(a))), m

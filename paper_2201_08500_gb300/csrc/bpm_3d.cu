@@ -81,13 +81,25 @@ struct Fft2Env {
     return s == 0 ? 0 : tw_off(s - 1) + 15 * Gm::LN(s - 1);
   }
 
+  // W_L(s)^(j m) of stage s for this thread (j = t % LN(s)): from the table,
+  // or, when LN(s) = 2 (the second stage of a 512-point transform), the
+  // W_32 powers as immediates selected by the lane parity (the same values).
+  template <int s>
+  static BPM_DEV float2 stage_tw(const float2* tw, int t, int m) {
+    constexpr int ln = Gm::LN(s);
+    if constexpr (ln == 2) {
+      const bool odd = t & 1;
+      return make_float2(odd ? w32_re(m) : 1.f, odd ? w32_im(m) : 0.f);
+    } else {
+      return __ldg(tw + tw_off(s) + (t % ln) + (m - 1) * ln);  // consecutive threads adjacent
+    }
+  }
+
   template <int s>
   static BPM_DEV void twid(float2 (&a)[16], float2 (&b)[16], const float2* tw, int t, bool inv) {
-    constexpr int ln = Gm::LN(s);
-    const float2* ts = tw + tw_off(s) + (t % ln);
 #pragma unroll
     for (int m = 1; m < 16; ++m) {
-      const float2 w = __ldg(ts + (m - 1) * ln);  // W_L(s)^(j m), consecutive threads adjacent
+      const float2 w = stage_tw<s>(tw, t, m);
       a[m] = inv ? c_mulc(a[m], w) : c_mul(a[m], w);
       b[m] = inv ? c_mulc(b[m], w) : c_mul(b[m], w);
     }
@@ -259,12 +271,15 @@ __global__ void __launch_bounds__(RT, 512 / RT) row_pass_kernel(Pass3DArgs A) {
     __syncthreads();  // the rows' exchange regions overlap the tile
     Fft2Env<NX>::template inv<-1>(a, b, xrow, 0, 0, A.twx, t, g);
     const float2* crow = A.cfield + (size_t(A.z) * A.ny + y) * NX;
+    const int2 sp = __ldg(A.cspan + size_t(A.z) * A.ny + y);  // crystal extent of the row
     const ChannelCoef cf = A.coef[ch];
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
       // c = 0 marks vacuum, where the coupling is the identity (warp-uniform
-      // except at the crystal's surfaces: a warp holds consecutive x)
-      const float2 c = __ldg(crow + t + T * k);
+      // except at the crystal's surfaces: a warp holds consecutive x); the row
+      // is loaded only inside its crystal extent
+      const int xk = t + T * k;
+      const float2 c = (xk >= sp.x && xk < sp.y) ? __ldg(crow + xk) : make_float2(0.f, 0.f);
       if (c.x == 0.f && c.y == 0.f) continue;
       const float ahx = cf.a_hi.x, ahy = cf.a_hi.y, alx = cf.a_lo.x, aly = cf.a_lo.y;
       const float2 bpc = c_mul(cf.bp, c);
@@ -376,11 +391,9 @@ struct Fft1Env {
 
   template <int s>
   static BPM_DEV void twid(float2 (&a)[16], const float2* tw, int t, bool inv) {
-    constexpr int ln = Gm::LN(s);
-    const float2* ts = tw + Fft2Env<N>::tw_off(s) + (t % ln);
 #pragma unroll
     for (int m = 1; m < 16; ++m) {
-      const float2 w = __ldg(ts + (m - 1) * ln);
+      const float2 w = Fft2Env<N>::template stage_tw<s>(tw, t, m);
       a[m] = inv ? c_mulc(a[m], w) : c_mul(a[m], w);
     }
   }

@@ -239,6 +239,7 @@ struct bpm_plan_s {
 
   // device buffers
   float2* cfield = nullptr;
+  int2* cspan = nullptr;  // 3D: [nz][ny] crystal extent of each deformation row
   float2* e0 = nullptr;
   float2* eh = nullptr;
   float4* tables = nullptr;
@@ -313,7 +314,8 @@ void free_plan_buffers(bpm_plan p) {
   void* ptrs[] = {p->cfield, p->e0,      p->eh,    p->tables, p->coef,     p->twiddle,
                   p->rev,    p->gain,    p->omega, p->weight, p->inc_norm, p->refl,
                   p->trans,  p->eh_time, p->dflag, p->u_tmp,  p->gcorr,    p->twy,
-                  p->qy,     p->spec,    p->twx3,  p->twiddle_t, p->twiddle_p, p->mask};
+                  p->qy,     p->spec,    p->twx3,  p->twiddle_t, p->twiddle_p, p->mask,
+                  p->cspan};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->ev0) cudaEventDestroy(p->ev0);
@@ -367,6 +369,7 @@ size_t plan_bytes(const bpm_grid& g, int n_ch) {
   const size_t nf = size_t(n_ch) * plane;
   size_t b = 0;
   b += size_t(g.nz) * plane * sizeof(float2);      // deformation factor
+  if (g.dims == 3) b += size_t(g.nz) * g.ny * sizeof(int2);  // its rows' crystal extents
   b += 2 * nf * sizeof(float2);                    // E0, Eh
   const size_t sets = g.split_order == 4 ? 2 : 1;   // table / coefficient sets per channel
   b += sets * n_ch * 2 * g.nx * sizeof(float4);     // propagator tables (3D: column anchors)
@@ -382,7 +385,13 @@ size_t plan_bytes(const bpm_grid& g, int n_ch) {
 }
 
 // Re-derive the deformation factor of the plan from its stored displacement.
-cudaError_t enqueue_crystal(bpm_plan p) { return launch_deformation(p->sa, p->u_dev, p->cfield, p->stream); }
+cudaError_t enqueue_crystal(bpm_plan p) {
+  cudaError_t e = launch_deformation(p->sa, p->u_dev, p->cfield, p->stream);
+  if (e != cudaSuccess || p->grid.dims != 3) return e;
+  // 3D: the row pass loads each deformation row only inside its crystal extent
+  return launch_crystal_span(p->cfield, p->grid.nx, (long long)p->grid.nz * p->grid.ny, p->cspan,
+                             p->stream);
+}
 
 // Tables, coefficients and incident field from the stored pulse; march back to z = 0.
 cudaError_t enqueue_pulse(bpm_plan p) {
@@ -454,6 +463,7 @@ BPM_API bpm_status bpm_plan_create(const bpm_grid* grid, int n_channels, void* c
     }
   };
   check(dalloc(&p->cfield, size_t(g.nz) * p->plane), "alloc deformation field");
+  if (g.dims == 3) check(dalloc(&p->cspan, size_t(g.nz) * g.ny), "alloc crystal extents");
   check(dalloc(&p->e0, nf), "alloc E0");
   check(dalloc(&p->eh, nf), "alloc Eh");
   const size_t sets = g.split_order == 4 ? 2 : 1;  // Eq. split-op order 4: two of each
@@ -779,6 +789,7 @@ BPM_API bpm_status bpm_run(bpm_plan p, int n_steps) {
     pa.s0 = p->spec;
     pa.sh = p->spec + size_t(p->n_ch) * p->plane;
     pa.cfield = p->cfield;
+    pa.cspan = p->cspan;
     pa.coef = p->coef;
     pa.twx = p->twx3;
     pa.twy = p->twy;

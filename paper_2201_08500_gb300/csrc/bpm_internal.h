@@ -78,6 +78,7 @@ struct Pass3DArgs {
   float2* s0;                // [n_ch][nx][ny] transposed x-spectrum (working buffers)
   float2* sh;
   const float2* cfield;      // [nz][ny][nx]
+  const int2* cspan;         // [nz][ny] {first, end} x of the nonzero cells of each row
   const ChannelCoef* coef;   // [n_ch]
   const float2* twx;         // stage twiddles of the x transform in thread order (twiddle_order)
   const float2* twy;         // same for the y transform
@@ -196,6 +197,13 @@ cudaError_t launch_reduce3d(const float2* e0, const float2* eh, long long plane,
 cudaError_t launch_tables3d(const SetupArgs& sa, const double* omega, const double* gainx,
                             const int* revx, float4* anchor, float* gcorr, ChannelCoef* coef,
                             cudaStream_t s);
+// Extent of the crystal in each of `rows` deformation rows of nx cells:
+// span[r] = {first x with c != 0, last such x + 1}, {0, 0} for a row without
+// crystal.  The 3D row pass loads a row's c only inside it (c = 0 outside).
+// (The 1D marches load their rows unconditionally: guarding those loads by
+// the extent measured slower there.)
+cudaError_t launch_crystal_span(const float2* cfield, int nx, long long rows, int2* span,
+                                cudaStream_t s);
 cudaError_t launch_deformation(const SetupArgs& sa, const double* u_dev, float2* cfield,
                                cudaStream_t s);
 cudaError_t launch_tables(const SetupArgs& sa, const double* omega, const double* gain,

@@ -108,6 +108,41 @@ __global__ void deformation_kernel(SetupArgs sa, const double* __restrict__ u, f
   }
 }
 
+// Crystal extent of each deformation row (one block per row at a time).
+__global__ void crystal_span_kernel(const float2* __restrict__ cfield, int nx, long long rows,
+                                    int2* span) {
+  __shared__ int slo[32], shi[32];
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const float2* row = cfield + r * nx;
+    int lo = nx, hi = -1;
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+      const float2 c = row[x];
+      if (c.x != 0.f || c.y != 0.f) {
+        lo = min(lo, x);
+        hi = max(hi, x);
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      lo = min(lo, __shfl_xor_sync(0xFFFFFFFFu, lo, off));
+      hi = max(hi, __shfl_xor_sync(0xFFFFFFFFu, hi, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      slo[threadIdx.x / 32] = lo;
+      shi[threadIdx.x / 32] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < int(blockDim.x / 32); ++w) {
+        lo = min(lo, slo[w]);
+        hi = max(hi, shi[w]);
+      }
+      span[r] = hi < 0 ? make_int2(0, 0) : make_int2(lo, hi + 1);
+    }
+    __syncthreads();
+  }
+}
+
 // Power series of J0(w) and G1(w) = 2 J1(w)/w in terms of w^2 (A&S 9.1.10).
 __device__ void bessel_j0_g1(dc w2, dc* j0, dc* g1) {
   const dc z = dscale(w2, -0.25);
@@ -361,6 +396,13 @@ cudaError_t launch_deformation(const SetupArgs& sa, const double* u_dev, float2*
   long long blocks = (total + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
   deformation_kernel<<<int(blocks), 256, 0, s>>>(sa, u_dev, cfield);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_crystal_span(const float2* cfield, int nx, long long rows, int2* span,
+                                cudaStream_t s) {
+  const long long blocks = rows < 152 * 16 ? rows : 152 * 16;
+  crystal_span_kernel<<<int(blocks), 256, 0, s>>>(cfield, nx, rows, span);
   return cudaGetLastError();
 }
 

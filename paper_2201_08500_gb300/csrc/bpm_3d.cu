@@ -69,8 +69,11 @@ BPM_DEV int tile_at(int c, int r) {
 
 // Paired (E0, Eh) transform of size N held by a group of T = N/16 threads, 16
 // values per thread and envelope.  `buf` is the group's exchange area: element p
-// of envelope e lives at buf[(swz(p) * stride) + e * estride].
-template <int N>
+// of envelope e lives at buf[(swz(p) * stride) + e * estride].  PA: butterfly
+// additions in packed FP32 (the column passes; the row pass, with more live
+// values, measured faster with scalar additions).  Both column-pass forms use
+// the same PA, so they compute bitwise the same fields.
+template <int N, bool PA = false>
 struct Fft2Env {
   using Gm = Geom<N>;
   static constexpr int T = Gm::T;
@@ -148,12 +151,12 @@ struct Fft2Env {
   template <int s>
   static BPM_DEV void sfwd(float2 (&a)[16], float2 (&b)[16], const float2* tw, int t) {
     if constexpr (s < S - 1) {
-      dft16_fwd<false>(a);
-      dft16_fwd<false>(b);
+      dft16_fwd<false, false, PA>(a);
+      dft16_fwd<false, false, PA>(b);
       twid<s>(a, b, tw, t, false);
     } else {
-      last_stage<Gm::RLAST, false, false>(a);
-      last_stage<Gm::RLAST, false, false>(b);
+      last_stage<Gm::RLAST, false, false, false, PA>(a);
+      last_stage<Gm::RLAST, false, false, false, PA>(b);
     }
   }
 
@@ -161,11 +164,11 @@ struct Fft2Env {
   static BPM_DEV void sinv(float2 (&a)[16], float2 (&b)[16], const float2* tw, int t) {
     if constexpr (s < S - 1) {
       twid<s>(a, b, tw, t, true);
-      dft16_inv<false>(a);
-      dft16_inv<false>(b);
+      dft16_inv<false, false, PA>(a);
+      dft16_inv<false, false, PA>(b);
     } else {
-      last_stage<Gm::RLAST, true, false>(a);
-      last_stage<Gm::RLAST, true, false>(b);
+      last_stage<Gm::RLAST, true, false, false, PA>(a);
+      last_stage<Gm::RLAST, true, false, false, PA>(b);
     }
   }
 
@@ -354,7 +357,7 @@ __global__ void __launch_bounds__(kColThreads, 2) col_pass_kernel(Pass3DArgs A) 
     a[k] = e0[t + T * k];
     b[k] = eh[t + T * k];
   }
-  Fft2Env<NY>::fwd(a, b, buf, 1, NY, A.twy, t, g);
+  Fft2Env<NY, true>::fwd(a, b, buf, 1, NY, A.twy, t, g);
   const float4 an0 = __ldg(A.anchor + (size_t(ch) * 2 + 0) * A.nx + cs);
   const float4 an1 = __ldg(A.anchor + (size_t(ch) * 2 + 1) * A.nx + cs);
   const float g0 = __ldg(A.gcorr + (size_t(ch) * 2 + 0) * A.nx + cs);
@@ -370,7 +373,7 @@ __global__ void __launch_bounds__(kColThreads, 2) col_pass_kernel(Pass3DArgs A) 
     const float2 f1 = make_float2(fmaf(-0.5f * c1r, c1r, qd.y), c1r);
     b[k] = make_float2(fmaf(v.x, f1.x, fmaf(-v.y, f1.y, v.x)), fmaf(v.x, f1.y, fmaf(v.y, f1.x, v.y)));
   }
-  Fft2Env<NY>::inv(a, b, buf, 1, NY, A.twy, t, g);
+  Fft2Env<NY, true>::inv(a, b, buf, 1, NY, A.twy, t, g);
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
     e0[t + T * k] = a[k];
@@ -381,8 +384,9 @@ __global__ void __launch_bounds__(kColThreads, 2) col_pass_kernel(Pass3DArgs A) 
 // Single-envelope transform of N points held by a group of T = N/16 threads,
 // exchanging through the group's own region of Pad<N>::kSlots 64-bit slots
 // (the padded layout of the 1D march: conflict-free, one base register per
-// pattern).  Butterflies, twiddles and their order are those of Fft2Env, so
-// every element is computed bitwise as there.
+// pattern).  Butterflies (with packed additions), twiddles and their order
+// are those of the column pass's Fft2Env<N, true>, so every element is
+// computed bitwise as there.
 template <int N>
 struct Fft1Env {
   using Gm = Geom<N>;
@@ -413,10 +417,10 @@ struct Fft1Env {
   template <int s>
   static BPM_DEV void sfwd(float2 (&a)[16], const float2* tw, int t) {
     if constexpr (s < S - 1) {
-      dft16_fwd<false>(a);
+      dft16_fwd<false, false, true>(a);
       twid<s>(a, tw, t, false);
     } else {
-      last_stage<Gm::RLAST, false, false>(a);
+      last_stage<Gm::RLAST, false, false, false, true>(a);
     }
   }
 
@@ -424,9 +428,9 @@ struct Fft1Env {
   static BPM_DEV void sinv(float2 (&a)[16], const float2* tw, int t) {
     if constexpr (s < S - 1) {
       twid<s>(a, tw, t, true);
-      dft16_inv<false>(a);
+      dft16_inv<false, false, true>(a);
     } else {
-      last_stage<Gm::RLAST, true, false>(a);
+      last_stage<Gm::RLAST, true, false, false, true>(a);
     }
   }
 

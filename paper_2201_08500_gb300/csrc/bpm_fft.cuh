@@ -248,10 +248,10 @@ BPM_DEV void dft4_bd(float2& a, float2& b, float2& c, float2& d) {
 // twiddles inside the second butterflies (fewer instructions; the march
 // kernels); otherwise each twiddle is rounded on its own (the 3D passes, where
 // the fused form cost registers and measured slower).
-template <bool FUSE = true, bool PJ = FUSE>
+template <bool FUSE = true, bool PJ = FUSE, bool PA = FUSE>
 BPM_DEV void dft16_fwd(float2 (&v)[16]) {
 #pragma unroll
-  for (int k2 = 0; k2 < 4; ++k2) dft4<false, PJ, FUSE>(v[k2], v[k2 + 4], v[k2 + 8], v[k2 + 12]);
+  for (int k2 = 0; k2 < 4; ++k2) dft4<false, PJ, PA>(v[k2], v[k2 + 4], v[k2 + 8], v[k2 + 12]);
   v[5] = w16<1, false>(v[5]);
   v[7] = w16<3, false>(v[7]);
   v[10] = w16<4, false>(v[10]);
@@ -271,7 +271,7 @@ BPM_DEV void dft16_fwd(float2 (&v)[16]) {
     v[14] = w16<6, false>(v[14]);
 #pragma unroll
     for (int m1 = 0; m1 < 4; ++m1)
-      dft4<false, PJ, FUSE>(v[4 * m1], v[4 * m1 + 1], v[4 * m1 + 2], v[4 * m1 + 3]);
+      dft4<false, PJ, PA>(v[4 * m1], v[4 * m1 + 1], v[4 * m1 + 2], v[4 * m1 + 3]);
   }
   // register 4 m1 + m2 holds y[m1 + 4 m2]: transpose (register renaming only)
   float2 o[16];
@@ -284,7 +284,7 @@ BPM_DEV void dft16_fwd(float2 (&v)[16]) {
 }
 
 // Exact adjoint of dft16_fwd (unnormalised inverse DFT): y[m] in v[m] -> x[k] in v[k].
-template <bool FUSE = true, bool PJ = FUSE>
+template <bool FUSE = true, bool PJ = FUSE, bool PA = FUSE>
 BPM_DEV void dft16_inv(float2 (&v)[16]) {
   float2 o[16];
 #pragma unroll
@@ -293,7 +293,7 @@ BPM_DEV void dft16_inv(float2 (&v)[16]) {
     for (int m2 = 0; m2 < 4; ++m2) o[4 * m1 + m2] = v[m1 + 4 * m2];
 #pragma unroll
   for (int m1 = 0; m1 < 4; ++m1)
-    dft4<true, PJ, FUSE>(o[4 * m1], o[4 * m1 + 1], o[4 * m1 + 2], o[4 * m1 + 3]);
+    dft4<true, PJ, PA>(o[4 * m1], o[4 * m1 + 1], o[4 * m1 + 2], o[4 * m1 + 3]);
   o[5] = w16<1, true>(o[5]);
   o[7] = w16<3, true>(o[7]);
   o[10] = w16<4, true>(o[10]);
@@ -311,7 +311,7 @@ BPM_DEV void dft16_inv(float2 (&v)[16]) {
     o[11] = w16<6, true>(o[11]);
     o[14] = w16<6, true>(o[14]);
 #pragma unroll
-    for (int k2 = 0; k2 < 4; ++k2) dft4<true, PJ, FUSE>(o[k2], o[k2 + 4], o[k2 + 8], o[k2 + 12]);
+    for (int k2 = 0; k2 < 4; ++k2) dft4<true, PJ, PA>(o[k2], o[k2 + 4], o[k2 + 8], o[k2 + 12]);
   }
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = o[i];
@@ -358,26 +358,26 @@ BPM_DEV void dft8_inv(float2 (&v)[16]) {
 }
 
 // Last-stage butterflies: 16/R independent R-point DFTs on consecutive registers.
-template <int R, bool INV, bool FUSE = true, bool PJ = FUSE>
+template <int R, bool INV, bool FUSE = true, bool PJ = FUSE, bool PA = FUSE>
 BPM_DEV void last_stage(float2 (&v)[16]) {
   if constexpr (R == 16) {
-    if (INV) dft16_inv<FUSE, PJ>(v); else dft16_fwd<FUSE, PJ>(v);
+    if (INV) dft16_inv<FUSE, PJ, PA>(v); else dft16_fwd<FUSE, PJ, PA>(v);
   } else if constexpr (R == 8) {
     if (INV) {
-      dft8_inv<0, PJ, FUSE>(v);
-      dft8_inv<8, PJ, FUSE>(v);
+      dft8_inv<0, PJ, PA>(v);
+      dft8_inv<8, PJ, PA>(v);
     } else {
-      dft8_fwd<0, PJ, FUSE>(v);
-      dft8_fwd<8, PJ, FUSE>(v);
+      dft8_fwd<0, PJ, PA>(v);
+      dft8_fwd<8, PJ, PA>(v);
     }
   } else if constexpr (R == 4) {
 #pragma unroll
     for (int g = 0; g < 4; ++g)
-      dft4<INV, PJ, FUSE>(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+      dft4<INV, PJ, PA>(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
   } else {
     static_assert(R == 2, "last-stage radix");
 #pragma unroll
-    for (int g = 0; g < 8; ++g) dft2<FUSE>(v[2 * g], v[2 * g + 1]);
+    for (int g = 0; g < 8; ++g) dft2<PA>(v[2 * g], v[2 * g + 1]);
   }
 }
 

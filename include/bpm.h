@@ -398,6 +398,21 @@ BPM_API bpm_status bpm_measure_peak(int kind, int iters, double* flop_per_s, flo
                                     void* cuda_stream);
 
 /* ---------------------------------------------------------------------------
+ * Check of the failure path of the kernels that wait on bulk copies (no
+ * counterpart in the paper).  Those waits are bounded: after a limit of polls
+ * the waiting threads record a status that bpm_sync reports as
+ * BPM_ERR_TIMEOUT, instead of spinning forever.  This call makes such a wait
+ * run out on purpose, without any copy in flight: one block's mbarrier
+ * expects 16 bytes that nothing delivers, and its threads wait with the same
+ * bounded wait at `poll_limit` polls.  *gave_up is set to 1 when the wait gave
+ * up and the status was recorded (the expected outcome), 0 otherwise.  The
+ * context stays usable.  Synchronous on cuda_stream; allocates nothing.
+ * Returns BPM_ERR_INVALID_ARG for a null output or poll_limit < 1,
+ * BPM_ERR_UNSUPPORTED without a GB300, BPM_ERR_CUDA if the launch fails.
+ * ------------------------------------------------------------------------- */
+BPM_API bpm_status bpm_check_bounded_wait(int poll_limit, int* gave_up, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free single-instance run.  The paper has no counterpart: this is
  * a deployment convenience of this library.
  *

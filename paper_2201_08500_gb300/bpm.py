@@ -30,7 +30,7 @@ EXPORTS = ("bpm_plan_create", "bpm_set_crystal", "bpm_set_pulse", "bpm_set_field
            "bpm_set_geometry", "bpm_batch_set_max_blocks", "bpm_batch_pending",
            "bpm_batch_graph_kernels", "bpm_get_launch", "bpm_set_launch", "bpm_tune",
            "bpm_tune_save", "bpm_tune_load", "bpm_tune_clear", "bpm_set_channel_shard",
-           "bpm_set_crystal_shape", "bpm_measure_peak")
+           "bpm_set_crystal_shape", "bpm_measure_peak", "bpm_check_bounded_wait")
 
 
 class BpmError(RuntimeError):
@@ -118,6 +118,7 @@ def load(path: str = LIB_PATH):
         "bpm_plan_bytes": ([ctypes.POINTER(Grid), _I, _I], ctypes.c_size_t),
         "bpm_measure_peak": ([_I, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_float), _P],
                              _I),
+        "bpm_check_bounded_wait": ([_I, ctypes.POINTER(_I), _P], _I),
         "bpm_batch_create": ([ctypes.c_size_t, _P, ctypes.POINTER(_P)], _I),
         "bpm_batch_submit": ([_P, _P, ctypes.POINTER(ctypes.c_uint64)], _I),
         "bpm_batch_step": ([_P, _I], _I),
@@ -531,3 +532,14 @@ def measure_peak(kind: int = BPM_PEAK_FP32, iters: int = 1 << 16, stream=None):
     if st != 0:
         raise BpmError(st, "bpm_measure_peak failed")
     return rate.value, ms.value
+
+
+def check_bounded_wait(poll_limit: int = 1 << 12, stream=None) -> bool:
+    """Make one bounded bulk-copy wait run out (bpm_check_bounded_wait): True
+    when it gave up and recorded the timeout status, as designed."""
+    L = load()
+    gave_up = ctypes.c_int()
+    st = L.bpm_check_bounded_wait(int(poll_limit), ctypes.byref(gave_up), _stream_handle(stream))
+    if st != 0:
+        raise BpmError(st, "bpm_check_bounded_wait failed")
+    return gave_up.value == 1

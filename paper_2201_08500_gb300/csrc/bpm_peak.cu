@@ -11,6 +11,7 @@
 
 #include "../../include/bpm.h"
 #include "bpm_internal.h"
+#include "bpm_tma.cuh"
 
 namespace bpm {
 namespace {
@@ -40,6 +41,26 @@ __global__ void __launch_bounds__(kPeakThreads) fma_chain_kernel(int iters, T a,
   for (int j = 0; j < kChains; ++j) s += x[j];
   if (s == T(-1.2345e-7)) g_peak_sink = double(s);
 }
+
+// The bounded wait of the bulk-copy kernels, made to run out: one block's
+// mbarrier is told to expect 16 bytes that no copy will bring, and every
+// thread waits on it with mbar_wait (the function the streamed column pass
+// uses) at `limit` polls; a thread that gives up records the status the
+// kernels record.  No copy is in flight, so the block exits cleanly.
+__global__ void bounded_wait_probe_kernel(uint32_t limit, int* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar, 16u);
+  __syncthreads();
+  if (!mbar_wait(&bar, 0u, limit)) atomicExch(status, kStatusTmaTimeout);
+}
+
+// Status word of the probe.
+__device__ int g_probe_status;
 
 }  // namespace
 }  // namespace bpm
@@ -78,6 +99,25 @@ BPM_API bpm_status bpm_measure_peak(int kind, int iters, double* flop_per_s, flo
   const double flop = 2.0 * kChains * kUnroll * double(iters) * double(grid.x) * kPeakThreads;
   *ms = t;
   *flop_per_s = flop / (double(t) * 1e-3);
+  return BPM_OK;
+}
+
+BPM_API bpm_status bpm_check_bounded_wait(int poll_limit, int* gave_up, void* cuda_stream) {
+  BPM_NVTX();
+  if (!gave_up || poll_limit < 1) return BPM_ERR_INVALID_ARG;
+  int sms = 0;
+  if (!device_ready(&sms)) return BPM_ERR_UNSUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  int* status = nullptr;
+  if (cudaGetSymbolAddress(reinterpret_cast<void**>(&status), g_probe_status) != cudaSuccess)
+    return BPM_ERR_CUDA;
+  if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return BPM_ERR_CUDA;
+  bounded_wait_probe_kernel<<<1, 64, 0, st>>>(uint32_t(poll_limit), status);
+  int h = 0;
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess ||
+      cudaMemcpy(&h, status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return BPM_ERR_CUDA;
+  *gave_up = h == kStatusTmaTimeout ? 1 : 0;
   return BPM_OK;
 }
 

@@ -73,8 +73,8 @@ BPM_TMA bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait for the phase of parity `parity` to complete; false on time-out.
-BPM_TMA bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kTmaSpinLimit; ++i)
+BPM_TMA bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit = kTmaSpinLimit) {
+  for (uint32_t i = 0; i < limit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }

@@ -22,3 +22,29 @@ def test_fp32_and_fp64_peaks_are_physical():
     assert ms64 > 0 and 0 < r64 < r32
     with pytest.raises(bpm.BpmError):
         bpm.measure_peak(7, 10)
+
+
+def test_a_bounded_copy_wait_gives_up_and_reports_without_hanging():
+    """The kernels that wait on bulk copies (the streamed 3D column pass) bound
+    every wait: here one such wait is made to run out on purpose (an mbarrier
+    expecting bytes that no copy brings), at a small poll limit.  It must give
+    up, record the status, and leave the context usable: a plan runs and
+    matches a plan run before the probe."""
+    import numpy as np
+    import torch
+    from paper_2201_08500_gb300 import workloads
+    torch.cuda.set_device(0)
+    w = workloads.tiny(n_ch=4)
+    w.nz = 20
+    w.u = None
+    before = bpm.plan_from_workload(w)
+    before.run()
+    before.sync()
+    ref = before.eh()
+    before.close()
+    assert bpm.check_bounded_wait(1 << 10) is True
+    after = bpm.plan_from_workload(w)
+    after.run()
+    after.sync()
+    assert np.array_equal(after.eh(), ref)
+    after.close()

@@ -73,10 +73,10 @@ EXECUTED_FLOPS = {
 }
 # DRAM bytes of one z step of the 3D workload (one streamed column pass, launch
 # form 1, + one MODE-1 row pass, 256-thread row tile), from the live launch
-# list of those launches with --cache-control none: 1065.5 + 1086.3 MB, the
-# algorithmic 64 B per cell-update (2147 MB) within 0.2 %.
-MEASURED_TRAFFIC_3D = {("large-3d-512x512-nz1000-ch128", 1, 256): (539.5e6 + 526.0e6 + 539.8e6
-                                                                     + 546.5e6)}
+# list of those launches with --cache-control none: 1066.2 + 1082.6 MB, the
+# algorithmic 64 B per cell-update (2147 MB) within 0.1 %.
+MEASURED_TRAFFIC_3D = {("large-3d-512x512-nz1000-ch128", 1, 256): (539.6e6 + 526.6e6 + 537.6e6
+                                                                     + 545.0e6)}
 
 
 def flops_per_cell(n: int, split_order: int = 1) -> float:

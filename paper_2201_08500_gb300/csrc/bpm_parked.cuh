@@ -100,14 +100,7 @@ struct Parked {
   static BPM_DEV void stage_fwd(float2 (&v)[16], const float4* tw, int t) {
     if constexpr (s < S - 1) {
       dft16_fwd<true, kPJ>(v);
-      if constexpr (kWide) {
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const float4 w = twiddle_pair<s>(tw, t, i);
-          v[2 * i + 1] = c_mul(v[2 * i + 1], make_float2(w.x, w.y));
-          if (i < 7) v[2 * i + 2] = c_mul(v[2 * i + 2], make_float2(w.z, w.w));
-        }
-      } else if constexpr (Gm::LN(s) == 2) {
+      if constexpr (Gm::LN(s) == 2) {
         // W_32^(j m), j = t % 2: ones on even lanes, the fixed W_32^m on odd
         // ones, as immediates selected per lane (no loads: the loaded twiddles
         // made this 512-thread kernel spill 300 B a thread; a branch on the
@@ -116,6 +109,13 @@ struct Parked {
 #pragma unroll
         for (int m = 1; m < 16; ++m)
           v[m] = c_mul(v[m], make_float2(odd ? w32_re(m) : 1.f, odd ? w32_im(m) : 0.f));
+      } else if constexpr (kWide) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float4 w = twiddle_pair<s>(tw, t, i);
+          v[2 * i + 1] = c_mul(v[2 * i + 1], make_float2(w.x, w.y));
+          if (i < 7) v[2 * i + 2] = c_mul(v[2 * i + 2], make_float2(w.z, w.w));
+        }
       } else {
         const float2* t1 = reinterpret_cast<const float2*>(tw);
 #pragma unroll
@@ -129,18 +129,18 @@ struct Parked {
   template <int s>
   static BPM_DEV void stage_inv(float2 (&v)[16], const float4* tw, int t) {
     if constexpr (s < S - 1) {
-      if constexpr (kWide) {
+      if constexpr (Gm::LN(s) == 2) {
+        const bool odd = t & 1;
+#pragma unroll
+        for (int m = 1; m < 16; ++m)
+          v[m] = c_mulc(v[m], make_float2(odd ? w32_re(m) : 1.f, odd ? w32_im(m) : 0.f));
+      } else if constexpr (kWide) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const float4 w = twiddle_pair<s>(tw, t, i);
           v[2 * i + 1] = c_mulc(v[2 * i + 1], make_float2(w.x, w.y));
           if (i < 7) v[2 * i + 2] = c_mulc(v[2 * i + 2], make_float2(w.z, w.w));
         }
-      } else if constexpr (Gm::LN(s) == 2) {
-        const bool odd = t & 1;
-#pragma unroll
-        for (int m = 1; m < 16; ++m)
-          v[m] = c_mulc(v[m], make_float2(odd ? w32_re(m) : 1.f, odd ? w32_im(m) : 0.f));
       } else {
         const float2* t1 = reinterpret_cast<const float2*>(tw);
 #pragma unroll

@@ -438,8 +438,8 @@ BPM_API bpm_status bpm_check_bounded_wait(int poll_limit, int* gave_up, void* cu
  * NULL (perfect crystal); omega and weight_re_im are host arrays as for
  * bpm_set_pulse.  Asynchronous on cuda_stream, except that omega,
  * weight_re_im and the FFT constants are copied into the array with
- * cudaMemcpyAsync from pageable host memory, so those copies are staged by
- * the driver before the call returns.  The call takes no sizes for the
+ * cudaMemcpyAsync from pageable host memory, which the CUDA runtime stages
+ * before the call returns.  The call takes no sizes for the
  * caller's buffers: they must hold at least the sizes above (the Python
  * binding checks them).
  *

@@ -874,17 +874,22 @@ def main():
     plan.close()
     del u_dev, flush
     if world == 1 and not args.no_extras:
+        # each section is reported on its own: one that fails records its
+        # error in the line instead of costing the others (or the main line)
         torch.cuda.empty_cache()
         jobs = OracleJobs(threads=max(1, (os.cpu_count() or 2) - 4))
         extras = {}
         t_x = time.perf_counter()
-        extras["batched"] = run_batched(args, world, rank, local, jobs)
-        torch.cuda.empty_cache()
-        extras["3d"] = run_3d(args, world, rank, local, jobs)
-        torch.cuda.empty_cache()
-        extras["served"] = run_served(args, world, rank, local, jobs)
-        for name in ("batched", "3d", "served"):
-            extras[name]["parity"] = jobs.result(name)
+        for name, fn in (("batched", run_batched), ("3d", run_3d), ("served", run_served)):
+            try:
+                extras[name] = fn(args, world, rank, local, jobs)
+            except Exception as e:  # noqa: BLE001 - reported in the line
+                extras[name] = {"error": repr(e)[:400]}
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+        for name in extras:
+            if "error" not in extras[name] and name in jobs.jobs:
+                extras[name]["parity"] = jobs.result(name)
         jobs.close()
         line.update(extras)
         line["extras_wall_s"] = time.perf_counter() - t_x

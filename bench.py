@@ -885,8 +885,12 @@ def main():
                 extras[name] = fn(args, world, rank, local, jobs)
             except Exception as e:  # noqa: BLE001 - reported in the line
                 extras[name] = {"error": repr(e)[:400]}
-            torch.cuda.synchronize()
-            torch.cuda.empty_cache()
+            try:
+                torch.cuda.synchronize()
+                torch.cuda.empty_cache()
+            except Exception as e:  # noqa: BLE001 - a lost context ends the sections
+                extras[name].setdefault("error", repr(e)[:400])
+                break
         for name in extras:
             if "error" not in extras[name] and name in jobs.jobs:
                 extras[name]["parity"] = jobs.result(name)

@@ -29,6 +29,7 @@
 // 1/(Nx Ny) and the x round-trip gain folded in) times
 // 1 + i c - c^2/2 - delta_y, where c = -dz qy^2 / (2K) (|c| < 1e-4 here, so the
 // dropped terms are below 1e-12) and delta_y removes the y round-trip gain.
+#include <cuda.h>  // CUtensorMap and its encoder's types (the encoder is fetched at run time)
 #include <cuda_runtime.h>
 
 #include "bpm_fft.cuh"
@@ -204,6 +205,22 @@ struct Fft2Env {
   }
 };
 
+// Eq. fov10 coupling of one cell (E0 = p, Eh = m) with c = Pi exp(i h u) != 0:
+// E0 <- a p + b+ c m, Eh <- a m + b- conj(c) p, a = a_hi + a_lo (both row
+// passes use this, so they compute bitwise the same fields).
+BPM_DEV void couple3d(float2& pa, float2& mb, float2 c, const ChannelCoef& cf) {
+  const float ahx = cf.a_hi.x, ahy = cf.a_hi.y, alx = cf.a_lo.x, aly = cf.a_lo.y;
+  const float2 bpc = c_mul(cf.bp, c);
+  const float2 bmc = c_mulc(cf.bm, c);
+  const float2 p = pa, m = mb;
+  pa = make_float2(
+      fmaf(ahx, p.x, fmaf(-ahy, p.y, fmaf(bpc.x, m.x, fmaf(-bpc.y, m.y, fmaf(alx, p.x, -aly * p.y))))),
+      fmaf(ahx, p.y, fmaf(ahy, p.x, fmaf(bpc.x, m.y, fmaf(bpc.y, m.x, fmaf(alx, p.y, aly * p.x))))));
+  mb = make_float2(
+      fmaf(ahx, m.x, fmaf(-ahy, m.y, fmaf(bmc.x, p.x, fmaf(-bmc.y, p.y, fmaf(alx, m.x, -aly * m.y))))),
+      fmaf(ahx, m.y, fmaf(ahy, m.x, fmaf(bmc.x, p.y, fmaf(bmc.y, p.x, fmaf(alx, m.y, aly * m.x))))));
+}
+
 // Row pass over R = RT / T rows y0 .. y0 + R - 1 of one channel (T = NX/16,
 // RT = 256 or 512 threads: the tile height, and with it the length R x 8 bytes
 // of every column segment the transposed load / store moves, is a tuning
@@ -284,16 +301,7 @@ __global__ void __launch_bounds__(RT, 512 / RT) row_pass_kernel(Pass3DArgs A) {
       const int xk = t + T * k;
       const float2 c = (xk >= sp.x && xk < sp.y) ? __ldg(crow + xk) : make_float2(0.f, 0.f);
       if (c.x == 0.f && c.y == 0.f) continue;
-      const float ahx = cf.a_hi.x, ahy = cf.a_hi.y, alx = cf.a_lo.x, aly = cf.a_lo.y;
-      const float2 bpc = c_mul(cf.bp, c);
-      const float2 bmc = c_mulc(cf.bm, c);
-      const float2 p = a[k], m = b[k];
-      a[k] = make_float2(
-          fmaf(ahx, p.x, fmaf(-ahy, p.y, fmaf(bpc.x, m.x, fmaf(-bpc.y, m.y, fmaf(alx, p.x, -aly * p.y))))),
-          fmaf(ahx, p.y, fmaf(ahy, p.x, fmaf(bpc.x, m.y, fmaf(bpc.y, m.x, fmaf(alx, p.y, aly * p.x))))));
-      b[k] = make_float2(
-          fmaf(ahx, m.x, fmaf(-ahy, m.y, fmaf(bmc.x, p.x, fmaf(-bmc.y, p.y, fmaf(alx, m.x, -aly * m.y))))),
-          fmaf(ahx, m.y, fmaf(ahy, m.x, fmaf(bmc.x, p.y, fmaf(bmc.y, p.x, fmaf(alx, m.y, aly * m.x))))));
+      couple3d(a[k], b[k], c, cf);
     }
   }
   if constexpr (MODE == 2) {
@@ -560,6 +568,149 @@ __global__ void __launch_bounds__(kColTmaThreads, kColTmaBlocksPerSm)
   }
 }
 
+// Row pass streamed by the copy engine (MODE 1 of launch form 2 of 3D plans):
+// inverse x, coupling, forward x of every row, tiles of R = RT / T rows in and
+// out through tensor copies.  Persistent: each block walks the tiles
+// (channel, y0) of the pass.  A tile of one envelope is the box {2R floats
+// (R rows of y), NX columns c} of the transposed spectrum [ch][c][y]; the copy
+// engine lays it in shared memory as NX segments of R x 8 bytes, 16-byte
+// chunks swizzled within each 32/64/128-byte span (the span is the segment),
+// so the row reads (one warp: 32 consecutive c of one row) and the output
+// writes spread over all banks.  While a block transforms one tile the next
+// one arrives in the stage buffer (one mbarrier phase a tile).  The output
+// tile goes into the rows' exchange regions once the forward transforms are
+// done and leaves by tensor stores; the next tile's first exchange waits
+// until those stores have read it.  Stage (2 x NX x R x 8 B) + exchange
+// regions (R x Pad<NX>::kSlots x 16 B): 67 KB for three blocks a SM at R x 8
+// = 32 or 64 bytes of 128-thread tiles, 134 KB for one block of 256 threads.
+// The arithmetic of every element is that of row_pass_kernel MODE 1.
+template <int NX, int RT>
+struct RowTma {
+  static constexpr int T = NX / 16;
+  static constexpr int R = RT / T;                           // rows a tile
+  static constexpr int kSeg = R * int(sizeof(float2));      // bytes of a column segment
+  static constexpr int kBoxC = NX < 256 ? NX : 256;          // columns a tensor copy
+  static constexpr int kBoxes = NX / kBoxC;
+  static constexpr uint32_t kPlane = uint32_t(NX) * kSeg;   // one envelope's tile
+  static constexpr uint32_t kStage = 2 * kPlane;
+  static constexpr uint32_t kXchg =
+      (uint32_t(R) * Pad<NX>::kSlots * uint32_t(sizeof(float4)) + 1023u) / 1024u * 1024u;
+  // 1 KB of slack aligns the stage to the swizzle pattern's 1024-byte period
+  static constexpr size_t kSmem = 1024 + size_t(kStage) + kXchg + 16;
+  static constexpr int kBlocksPerSm = kSmem <= 70 * 1024 ? 3 : 1;
+  static_assert(kSeg == 32 || kSeg == 64 || kSeg == 128, "segment = swizzle span");
+  static_assert(kXchg >= kStage, "the output tile fits in the exchange regions");
+  static_assert(kSmem <= 227 * 1024, "shared memory of a block");
+
+  // Byte offset of element (c, r) in an envelope's tile: the copy engine's
+  // swizzle (16-byte chunk index XOR bits 7.. of the offset, as many bits as
+  // the span has chunks minus one).
+  static BPM_DEV uint32_t at(int c, int r) {
+    const uint32_t lin = uint32_t(c) * uint32_t(kSeg) + uint32_t(r) * 8u;
+    return lin ^ (((lin >> 7) & uint32_t(kSeg / 16 - 1)) << 4);
+  }
+};
+
+template <int NX, int RT>
+__global__ void __launch_bounds__(RT, RowTma<NX, RT>::kBlocksPerSm)
+    row_pass_tma_kernel(const __grid_constant__ CUtensorMap map0,
+                        const __grid_constant__ CUtensorMap maph, Pass3DArgs A, int n_ch,
+                        int* status) {
+  using L = RowTma<NX, RT>;
+  constexpr int T = L::T;
+  constexpr int R = L::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* stage = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+  unsigned char* xreg = stage + L::kStage;  // exchange regions, then the output tile
+  uint64_t* bar = reinterpret_cast<uint64_t*>(xreg + L::kXchg);
+  const int g = threadIdx.x / T;  // row of the tile
+  const int t = threadIdx.x % T;
+  float2* xrow = reinterpret_cast<float2*>(reinterpret_cast<float4*>(xreg) + size_t(g) * Pad<NX>::kSlots);
+  const int tiles_per_ch = A.ny / R;
+  const int n_tiles = n_ch * tiles_per_ch;
+  // one thread: announce and issue the tensor copies of tile `tile`
+  auto issue = [&](int tile) {
+    const int cy = (tile / tiles_per_ch) * NX;
+    const int x = 2 * (tile % tiles_per_ch) * R;
+    mbar_arrive_expect_tx(bar, L::kStage);
+#pragma unroll
+    for (int bx = 0; bx < L::kBoxes; ++bx) {
+      tma_load_2d(stage + bx * L::kBoxC * L::kSeg, &map0, x, cy + bx * L::kBoxC, bar);
+      tma_load_2d(stage + L::kPlane + bx * L::kBoxC * L::kSeg, &maph, x, cy + bx * L::kBoxC, bar);
+    }
+  };
+  int tile = blockIdx.x;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_init_fence();
+    if (tile < n_tiles) issue(tile);
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  for (; tile < n_tiles; tile += gridDim.x) {
+    if (!__syncthreads_and(mbar_wait(bar, phase))) {
+      if (threadIdx.x == 0) {
+        atomicExch(status, kStatusTmaTimeout);
+        mbar_wait(bar, phase);  // the tile still in flight, bounded
+        bulk_wait_all();
+      }
+      return;
+    }
+    phase ^= 1u;
+    float2 a[16], b[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const uint32_t o = L::at(k * T + t, g);
+      a[k] = *reinterpret_cast<const float2*>(stage + o);
+      b[k] = *reinterpret_cast<const float2*>(stage + L::kPlane + o);
+    }
+    const int ch = tile / tiles_per_ch;
+    const int y0 = (tile % tiles_per_ch) * R;
+    const int y = y0 + g;
+    // the row's deformation factor, loaded under the inverse transform (zero
+    // outside the row's crystal extent, where the coupling is the identity)
+    const float2* crow = A.cfield + (size_t(A.z) * A.ny + y) * NX;
+    const int2 sp = __ldg(A.cspan + size_t(A.z) * A.ny + y);
+    float2 cv[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int xk = t + T * k;
+      cv[k] = (xk >= sp.x && xk < sp.y) ? __ldg(crow + xk) : make_float2(0.f, 0.f);
+    }
+    if (threadIdx.x == 0) bulk_wait_read_all();  // the last tile's stores have read xreg
+    __syncthreads();  // every read of the stage is done; xreg is free
+    if (threadIdx.x == 0 && tile + int(gridDim.x) < n_tiles) {
+      fence_proxy_async_smem();
+      issue(tile + gridDim.x);
+    }
+    Fft2Env<NX>::template inv<-1>(a, b, xrow, 0, 0, A.twx, t, g);
+    const ChannelCoef cf = A.coef[ch];
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if (cv[k].x != 0.f || cv[k].y != 0.f) couple3d(a[k], b[k], cv[k], cf);
+    Fft2Env<NX>::template fwd<-1>(a, b, xrow, 0, 0, A.twx, t, g);
+    __syncthreads();  // every row is done with its exchange region
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const uint32_t o = L::at(k * T + t, g);
+      *reinterpret_cast<float2*>(xreg + o) = a[k];
+      *reinterpret_cast<float2*>(xreg + L::kPlane + o) = b[k];
+    }
+    fence_proxy_async_smem();  // this thread's writes, before the copy engine reads them
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int cy = ch * NX;
+#pragma unroll
+      for (int bx = 0; bx < L::kBoxes; ++bx) {
+        tma_store_2d(&map0, 2 * y0, cy + bx * L::kBoxC, xreg + bx * L::kBoxC * L::kSeg);
+        tma_store_2d(&maph, 2 * y0, cy + bx * L::kBoxC, xreg + L::kPlane + bx * L::kBoxC * L::kSeg);
+      }
+      bulk_commit();
+    }
+  }
+  if (threadIdx.x == 0) bulk_wait_all();
+}
+
 // Per-channel sums of |E0|^2 and |Eh|^2 over the plane (FP64), divided by the
 // incident norm.
 __global__ void reduce3d_kernel(const float2* e0, const float2* eh, long long plane,
@@ -640,6 +791,68 @@ cudaError_t col_tma_launch(const Pass3DArgs& a, int n_ch, int sms, int* status, 
   return cudaGetLastError();
 }
 
+// cuTensorMapEncodeTiled, fetched from the driver through the runtime (no
+// link-time dependency on the driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static const EncodeTiledFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return EncodeTiledFn(nullptr);
+    return reinterpret_cast<EncodeTiledFn>(f);
+  }();
+  return fn;
+}
+
+// Tensor map of one envelope's transposed spectrum [n_ch * NX][ny] complex64
+// as FP32 pairs, boxes of the streamed row pass's tile.
+template <int NX, int RT>
+bool encode_row_map(CUtensorMap* m, float2* base, int ny, int n_ch) {
+  using L = RowTma<NX, RT>;
+  const EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {cuuint64_t(2) * ny, cuuint64_t(NX) * n_ch};
+  const cuuint64_t strides[1] = {cuuint64_t(ny) * sizeof(float2)};
+  const cuuint32_t box[2] = {cuuint32_t(2 * L::R), cuuint32_t(L::kBoxC)};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUtensorMapSwizzle sw = L::kSeg == 32   ? CU_TENSOR_MAP_SWIZZLE_32B
+                                : L::kSeg == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                : CU_TENSOR_MAP_SWIZZLE_128B;
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int NX, int RT>
+cudaError_t row_tma_launch(const Pass3DArgs& a, int n_ch, int sms, int* status, cudaStream_t s) {
+  using L = RowTma<NX, RT>;
+  if (a.ny % L::R != 0) return cudaErrorInvalidValue;
+  CUtensorMap m0, mh;
+  if (!encode_row_map<NX, RT>(&m0, a.s0, a.ny, n_ch) ||
+      !encode_row_map<NX, RT>(&mh, a.sh, a.ny, n_ch))
+    return cudaErrorInvalidValue;
+  const long long tiles = (long long)n_ch * (a.ny / L::R);
+  const long long cap = (long long)sms * L::kBlocksPerSm;
+  const int blocks = int(tiles < cap ? tiles : cap);
+  if (blocks == 0) return cudaSuccess;
+  row_pass_tma_kernel<NX, RT><<<blocks, RT, L::kSmem, s>>>(m0, mh, a, n_ch, status);
+  return cudaGetLastError();
+}
+
+template <int NX, int RT>
+cudaError_t row_tma_attrs() {
+  return cudaFuncSetAttribute(row_pass_tma_kernel<NX, RT>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(RowTma<NX, RT>::kSmem));
+}
+
 template <int NX, int RT>
 cudaError_t row_attrs() {
   cudaError_t e = cudaSuccess, r;
@@ -684,7 +897,25 @@ cudaError_t pass3d_set_attributes() {
   if ((r = col_attrs<256>()) != cudaSuccess) e = r;
   if ((r = col_attrs<512>()) != cudaSuccess) e = r;
   if ((r = col_attrs<1024>()) != cudaSuccess) e = r;
+  if ((r = row_tma_attrs<256, 128>()) != cudaSuccess) e = r;
+  if ((r = row_tma_attrs<512, 128>()) != cudaSuccess) e = r;
+  if ((r = row_tma_attrs<512, 256>()) != cudaSuccess) e = r;
+  if ((r = row_tma_attrs<1024, 256>()) != cudaSuccess) e = r;
   return e;
+}
+
+bool row_tma_supported(int nx, int row_threads) {
+  return (nx == 256 && row_threads == 128) || (nx == 512 && (row_threads == 128 || row_threads == 256)) ||
+         (nx == 1024 && row_threads == 256);
+}
+
+cudaError_t launch_row_pass_tma(int row_threads, const Pass3DArgs& a, int n_ch, int sms,
+                                int* status, cudaStream_t s) {
+  if (a.nx == 256 && row_threads == 128) return row_tma_launch<256, 128>(a, n_ch, sms, status, s);
+  if (a.nx == 512 && row_threads == 128) return row_tma_launch<512, 128>(a, n_ch, sms, status, s);
+  if (a.nx == 512 && row_threads == 256) return row_tma_launch<512, 256>(a, n_ch, sms, status, s);
+  if (a.nx == 1024 && row_threads == 256) return row_tma_launch<1024, 256>(a, n_ch, sms, status, s);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_row_pass(int mode, int row_threads, const Pass3DArgs& a, int n_ch,
@@ -703,7 +934,7 @@ cudaError_t launch_row_pass(int mode, int row_threads, const Pass3DArgs& a, int 
 
 cudaError_t launch_col_pass(int form, const Pass3DArgs& a, int n_ch, int sms, int* status,
                             cudaStream_t s) {
-  if (form == 1) {
+  if (form >= 1) {
     if (a.ny == 256) return col_tma_launch<256>(a, n_ch, sms, status, s);
     if (a.ny == 512) return col_tma_launch<512>(a, n_ch, sms, status, s);
     if (a.ny == 1024) return col_tma_launch<1024>(a, n_ch, sms, status, s);

@@ -341,7 +341,8 @@ TuneKey tune_key(const bpm_grid& g, int n_ch) {
 // Whether a plan of grid g can run launch form (form, group, row_threads).
 bool launch_valid(const bpm_grid& g, int form, int group, int row_threads) {
   if (g.dims == 3)
-    return (form == 0 || form == 1) && group == 1 && (row_threads == 256 || row_threads == 512);
+    return group == 1 && (((form == 0 || form == 1) && (row_threads == 256 || row_threads == 512)) ||
+                          (form == 2 && row_tma_supported(g.nx, row_threads)));
   const int maxg = march_max_group(g.nx);
   if (row_threads != 256) return false;
   if (form == 0) return group == 1 || group == maxg;
@@ -799,14 +800,23 @@ BPM_API bpm_status bpm_run(bpm_plan p, int n_steps) {
     pa.nx = p->grid.nx;
     pa.ny = p->grid.ny;
     pa.z = p->z;
-    BPM_CUDA(p, launch_row_pass(0, p->row_threads, pa, p->n_ch, p->stream), "row pass");
+    // form 2 streams the MODE-1 row passes; its first and last row passes
+    // (once a run) are the plain ones with 256-thread tiles
+    const int plain_rt = p->form == 2 ? 256 : p->row_threads;
+    const int sms = device_info().sm_count;
+    BPM_CUDA(p, launch_row_pass(0, plain_rt, pa, p->n_ch, p->stream), "row pass");
     march_launches = 1;
     for (int s = 0; s < n_steps; ++s) {
       pa.z = p->z + s;
-      BPM_CUDA(p, launch_col_pass(p->form, pa, p->n_ch, device_info().sm_count, p->dflag + 1,
-                                  p->stream),
+      BPM_CUDA(p, launch_col_pass(p->form, pa, p->n_ch, sms, p->dflag + 1, p->stream),
                "column pass");
-      BPM_CUDA(p, launch_row_pass(s == n_steps - 1 ? 2 : 1, p->row_threads, pa, p->n_ch, p->stream), "row pass");
+      if (s == n_steps - 1)
+        BPM_CUDA(p, launch_row_pass(2, plain_rt, pa, p->n_ch, p->stream), "row pass");
+      else if (p->form == 2)
+        BPM_CUDA(p, launch_row_pass_tma(p->row_threads, pa, p->n_ch, sms, p->dflag + 1, p->stream),
+                 "row pass");
+      else
+        BPM_CUDA(p, launch_row_pass(1, plain_rt, pa, p->n_ch, p->stream), "row pass");
       march_launches += 2;
     }
   }
@@ -851,13 +861,13 @@ BPM_API bpm_status bpm_sync(bpm_plan p) {
   BPM_NVTX();
   if (!p) return fail(nullptr, BPM_ERR_INVALID_ARG, "null plan");
   BPM_CUDA(p, cudaStreamSynchronize(p->stream), "stream synchronize");
-  if (p->grid.dims == 3 && p->form == 1) {
-    // status word of the streamed column pass: a bounded wait that gave up
+  if (p->grid.dims == 3 && p->form >= 1) {
+    // status word of the streamed passes: a bounded wait that gave up
     int st = 0;
     BPM_CUDA(p, cudaMemcpy(&st, p->dflag + 1, sizeof(int), cudaMemcpyDeviceToHost), "status");
     if (st != 0) {
       BPM_CUDA(p, cudaMemset(p->dflag + 1, 0, sizeof(int)), "clear status");
-      return fail(p, BPM_ERR_TIMEOUT, "3D column pass: a bulk-copy wait gave up");
+      return fail(p, BPM_ERR_TIMEOUT, "3D streamed pass: a bulk-copy wait gave up");
     }
   }
   return BPM_OK;
@@ -1027,6 +1037,8 @@ BPM_API bpm_status bpm_tune(const bpm_grid* grid, int n_channels, int steps, bpm
       cand.push_back(bpm_launch{0, 1, 512, 0.f});
       cand.push_back(bpm_launch{1, 1, 256, 0.f});
       cand.push_back(bpm_launch{1, 1, 512, 0.f});
+      for (int rt : {128, 256})
+        if (launch_valid(g, 2, 1, rt)) cand.push_back(bpm_launch{2, 1, rt, 0.f});
     } else {
       const int maxg = march_max_group(g.nx);
       cand.push_back(bpm_launch{0, 1, 256, 0.f});

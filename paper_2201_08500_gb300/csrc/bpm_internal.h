@@ -185,11 +185,17 @@ cudaError_t pass3d_set_attributes();
 // row_threads: 256 or 512 (tile of 256/T or 512/T rows, T = nx/16)
 cudaError_t launch_row_pass(int mode, int row_threads, const Pass3DArgs& a, int n_ch,
                             cudaStream_t s);
-// form 0: one block per column group; form 1: the persistent column pass
+// form 0: one block per column group; form >= 1: the persistent column pass
 // streamed by bulk copies (sms: the SM count; status: device word that a
 // bounded wait which gave up sets to kStatusTmaTimeout)
 cudaError_t launch_col_pass(int form, const Pass3DArgs& a, int n_ch, int sms, int* status,
                             cudaStream_t s);
+// The MODE-1 row pass streamed by tensor copies (launch form 2): tiles of
+// row_threads / (nx/16) rows, for (nx, row_threads) = (256, 128), (512, 128),
+// (512, 256), (1024, 256); sms and status as for the column pass.
+bool row_tma_supported(int nx, int row_threads);
+cudaError_t launch_row_pass_tma(int row_threads, const Pass3DArgs& a, int n_ch, int sms,
+                                int* status, cudaStream_t s);
 cudaError_t launch_reduce3d(const float2* e0, const float2* eh, long long plane, int n_ch,
                             const double* inc, double* refl, double* trans, cudaStream_t s);
 

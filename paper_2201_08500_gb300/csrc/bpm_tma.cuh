@@ -60,6 +60,35 @@ BPM_TMA void bulk_load(void* smem_dst, const void* gmem_src, uint32_t bytes, uin
       : "memory");
 }
 
+// Tiled 2D tensor copy global -> shared of the box at element coordinates
+// (x, y) of the tensor map (a __grid_constant__ kernel parameter), completing
+// on `bar`.  x times the element size must be a multiple of 16 bytes.
+BPM_TMA void tma_load_2d(void* smem_dst, const void* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(smem_addr(smem_dst)), "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Tiled 2D tensor copy shared -> global of the box at (x, y), x >= 0 and
+// y >= 0, in the current bulk group of this thread.
+BPM_TMA void tma_store_2d(const void* map, int x, int y, const void* smem_src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];"
+               ::"l"(map), "r"(x), "r"(y), "r"(smem_addr(smem_src))
+               : "memory");
+}
+
+// Closes this thread's current bulk group of stores.
+BPM_TMA void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+// Waits until every committed store group of this thread has read its shared
+// memory (the source may then be rewritten).
+BPM_TMA void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
+// Waits until every committed store group of this thread is complete.
+BPM_TMA void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 BPM_TMA bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t done;
   asm volatile(

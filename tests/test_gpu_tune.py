@@ -95,6 +95,30 @@ def test_3d_streamed_column_pass_gives_identical_fields(nx, ny, n_ch):
         assert np.array_equal(a[k], b[k]), k
 
 
+@pytest.mark.parametrize("nx,ny,n_ch,rt", [(512, 512, 8, 128), (512, 512, 5, 256),
+                                           (256, 512, 9, 128), (1024, 256, 4, 256),
+                                           (512, 256, 1, 128)])
+def test_3d_streamed_row_pass_gives_identical_fields(nx, ny, n_ch, rt):
+    """Launch form 2 of a 3D plan: the MODE-1 row passes stream their tiles in
+    and out with tensor copies (swizzled boxes of rt / (nx/16) rows), the next
+    tile arriving while the current one is transformed.  Same arithmetic per
+    element as form 0, so the fields are bitwise equal.  The channel counts
+    give most blocks of the persistent grid two or three tiles (the prefetch
+    and the mbarrier phases) with a ragged end; the last case fills only part
+    of the grid."""
+    from test_gpu_3d import case3d
+    w = case3d(nx, ny, 12, n_ch, seed=nx + ny + n_ch + rt)
+    a, used_a = fields(w, form=0, row_threads=256)
+    b, used_b = fields(w, form=2, row_threads=rt)
+    assert used_a["form"] == 0 and used_b["form"] == 2 and used_b["row_threads"] == rt
+    for k in ("e0", "eh", "R"):
+        assert np.array_equal(a[k], b[k]), k
+    p = bpm.plan_from_workload(w)
+    with pytest.raises(bpm.BpmError):
+        p.set_launch(form=2, row_threads=512)  # no streamed tile of 512 threads
+    p.close()
+
+
 def test_3d_row_tiles_give_identical_fields():
     from test_gpu_3d import case3d
     w = case3d(512, 256, 16, 2, seed=5)
@@ -141,6 +165,6 @@ def test_tuner_keeps_the_fastest_and_later_plans_use_it(tmp_path):
     assert q.launch() == want
     q.close()
     b3, every3 = bpm.tune(3, 256, 256, 1e-6, 1e-6, 0.25e-6, 2, steps=4)
-    assert {f["row_threads"] for f in every3} == {256, 512}
-    assert {f["form"] for f in every3} == {0, 1}
+    assert {f["row_threads"] for f in every3} == {128, 256, 512}
+    assert {f["form"] for f in every3} == {0, 1, 2}
     bpm.tune_clear()

@@ -76,7 +76,9 @@ EXECUTED_FLOPS = {
 # list of those launches with --cache-control none: 1066.2 + 1082.6 MB, the
 # algorithmic 64 B per cell-update (2147 MB) within 0.1 %.
 MEASURED_TRAFFIC_3D = {("large-3d-512x512-nz1000-ch128", 1, 256): (539.6e6 + 526.6e6 + 537.6e6
-                                                                     + 545.0e6)}
+                                                                     + 545.0e6),
+                       ("large-3d-512x512-nz1000-ch128", 2, 128): (539.5e6 + 528.3e6 + 539.3e6
+                                                                     + 544.7e6)}
 
 
 def flops_per_cell(n: int, split_order: int = 1) -> float:
@@ -451,7 +453,7 @@ def run_3d(args, world, rank, local, jobs=None):
     plan = bpm.Plan(w.dims, w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.n_ch, stream=stream)
     plan.set_timing(True)
     if args.launch_form is not None:
-        plan.set_launch(form=args.launch_form)
+        plan.set_launch(form=args.launch_form, row_threads=args.row_threads)
 
     def step():
         plan.set_crystal(w.chi0, w.chih, w.chihb, w.theta_B, w.lambda_B, w.x_surface,
@@ -494,7 +496,10 @@ def run_3d(args, world, rank, local, jobs=None):
                          (w.name, launch["form"], launch["row_threads"])),
                      "traffic_unit": "one z step: column pass + row pass",
                      "algorithmic_bytes": 64 * w.n_ch * w.plane,
-                     "kernel": "row_pass_kernel + col_pass_kernel (2 passes per z step)",
+                     "kernel": {0: "row_pass_kernel + col_pass_kernel",
+                                1: "row_pass_kernel + col_pass_tma_kernel",
+                                2: "row_pass_tma_kernel + col_pass_tma_kernel"}[launch["form"]]
+                               + " (2 passes per z step)",
                      "bytes_per_cell_update": 64, "march_ms": march_ms,
                      "passes": st["march_launches"]},
         "gpu_launches": (st["launches"] + 4) * steps, "clocks": clocks,
@@ -663,6 +668,8 @@ def main():
                     help="channels of the deformed workload (profiling: a smaller instance)")
     ap.add_argument("--nz", type=int, default=2000, help="z steps of the deformed workload")
     ap.add_argument("--nx", type=int, default=4096, help="transform size of the deformed workload")
+    ap.add_argument("--row-threads", type=int, default=None, choices=[128, 256, 512],
+                    help="with --launch-form on the 3d workload: the row-pass tile")
     ap.add_argument("--launch-form", type=int, default=None, choices=[0, 1, 2, 3],
                     help="force a launch form of the deformed workload's march (default: "
                          "the autotuner's choice)")

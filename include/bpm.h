@@ -238,9 +238,17 @@ BPM_API bpm_status bpm_get_stats(bpm_plan plan, bpm_stats* out);
  *                      3 = parked with the tables in tensor memory (TMEM)
  *                      instead of L2 (first order or Strang, Nx = 2048, 4096,
  *                      8192, channels_per_block = 1).
+ *                      3D passes: 0 = one block per column group and per row
+ *                      tile; 1 = the column pass persistent, each column
+ *                      streamed in by a bulk copy; 2 = form 1 plus the
+ *                      inner row passes persistent, their tiles streamed in
+ *                      and out by tensor copies (row_threads 128 at
+ *                      nx = 256, 128 or 256 at nx = 512, 256 at nx = 1024);
+ *                      channels_per_block = 1.
  *   channels_per_block 2D march: 1, or the maximum of the size (16, 8, 4, 2, 1
  *                      for Nx = 256, 512, 1024, 2048, >= 4096).
- *   row_threads        3D row pass: 256 or 512 threads per block, i.e. a tile
+ *   row_threads        3D row pass: 256 or 512 threads per block (form 2:
+ *                      see above; its first and last row pass use 256), i.e. a tile
  *                      of 256/T or 512/T rows (T = nx/16); taller tiles move
  *                      longer column segments in the transposed store.
  *   ms                 bpm_tune: median time of `steps` steps in this form. */

@@ -102,13 +102,18 @@ struct Parked {
       dft16_fwd<true, kPJ>(v);
       if constexpr (Gm::LN(s) == 2) {
         // W_32^(j m), j = t % 2: ones on even lanes, the fixed W_32^m on odd
-        // ones, as immediates selected per lane (no loads: the loaded twiddles
-        // made this 512-thread kernel spill 300 B a thread; a branch on the
-        // lane parity instead of the selection measured slower than both)
-        const bool odd = t & 1;
+        // ones, as immediates (no loads: the loaded twiddles made this
+        // 512-thread kernel spill 300 B a thread).  Where the lane-pair swap
+        // follows this stage they are applied after it (pair_twiddle: the
+        // same constants on the same values, only the products by one left
+        // out); otherwise selected per lane here (a branch on the lane
+        // parity measured slower than the selection).
+        if constexpr (!(kPairLast && s == S - 2)) {
+          const bool odd = t & 1;
 #pragma unroll
-        for (int m = 1; m < 16; ++m)
-          v[m] = c_mul(v[m], make_float2(odd ? w32_re(m) : 1.f, odd ? w32_im(m) : 0.f));
+          for (int m = 1; m < 16; ++m)
+            v[m] = c_mul(v[m], make_float2(odd ? w32_re(m) : 1.f, odd ? w32_im(m) : 0.f));
+        }
       } else if constexpr (kWide) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -130,10 +135,12 @@ struct Parked {
   static BPM_DEV void stage_inv(float2 (&v)[16], const float4* tw, int t) {
     if constexpr (s < S - 1) {
       if constexpr (Gm::LN(s) == 2) {
-        const bool odd = t & 1;
+        if constexpr (!(kPairLast && s == S - 2)) {  // see stage_fwd
+          const bool odd = t & 1;
 #pragma unroll
-        for (int m = 1; m < 16; ++m)
-          v[m] = c_mulc(v[m], make_float2(odd ? w32_re(m) : 1.f, odd ? w32_im(m) : 0.f));
+          for (int m = 1; m < 16; ++m)
+            v[m] = c_mulc(v[m], make_float2(odd ? w32_re(m) : 1.f, odd ? w32_im(m) : 0.f));
+        }
       } else if constexpr (kWide) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -194,6 +201,22 @@ struct Parked {
       if (odd) v[i] = r; else v[8 + i] = r;
     }
   }
+  // The W_32 twiddles of stage S-2 on the swapped arrangement: before the
+  // swap, odd lanes multiply their value m by W_32^m and even lanes by one;
+  // after it, those products are exactly the values in v[8+i] (the even
+  // lane's came from the odd lane's v[i], the odd lane's are its own v[8+i]),
+  // so 8 products a thread replace 15.  INV: the conjugates, applied before
+  // the swap that restores stage S-2.
+  template <bool INV>
+  static BPM_DEV void pair_twiddle(float2 (&v)[16], int t) {
+    const bool odd = t & 1;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float2 w = make_float2(odd ? w32_re(8 + i) : (i == 0 ? 1.f : w32_re(i)),
+                                   odd ? w32_im(8 + i) : (i == 0 ? 0.f : w32_im(i)));
+      v[8 + i] = INV ? c_mulc(v[8 + i], w) : c_mul(v[8 + i], w);
+    }
+  }
 
   // Table multiply of one envelope: 16 positions, hi/lo float4 each, from L2
   // (gt) or from this thread's TMEM columns (tcol).
@@ -229,6 +252,7 @@ struct Parked {
     stage_fwd<2>(v, tw, t);
     if constexpr (kPairLast) {
       pair_swap(v, t);
+      pair_twiddle<false>(v, t);
       float2 w[16];  // stage-3 register order (a renaming, no data movement)
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
@@ -243,6 +267,7 @@ struct Parked {
         v[i] = w[2 * i];
         v[8 + i] = w[2 * i + 1];
       }
+      pair_twiddle<true>(v, t);
       pair_swap(v, t);
     } else {
       multiply(v, gt, tcol, t);

@@ -79,6 +79,10 @@ struct Fft2Env {
   using Gm = Geom<N>;
   static constexpr int T = Gm::T;
   static constexpr int S = Gm::S;
+  // N = 512 (16 x 16 x 2): the second stage's twiddles W_32^(j m), j = t % 2,
+  // are applied on the other side of the exchange into the radix-2 last
+  // stage (twid_last), where they fall on 8 values a thread instead of 15.
+  static constexpr bool kTwAfter = (S == 3 && Gm::LN(1) == 2);
 
   // Offset of stage s in the thread-ordered twiddle table (see twiddle_order).
   __host__ __device__ static constexpr int tw_off(int s) {
@@ -101,11 +105,32 @@ struct Fft2Env {
 
   template <int s>
   static BPM_DEV void twid(float2 (&a)[16], float2 (&b)[16], const float2* tw, int t, bool inv) {
+    if constexpr (kTwAfter && s == 1) return;  // see twid_last
 #pragma unroll
     for (int m = 1; m < 16; ++m) {
       const float2 w = stage_tw<s>(tw, t, m);
       a[m] = inv ? c_mulc(a[m], w) : c_mul(a[m], w);
       b[m] = inv ? c_mulc(b[m], w) : c_mul(b[m], w);
+    }
+  }
+
+  // W_32 factor, in the last stage's layout, of value k = 2i + 1 of thread t:
+  // position 16 t + k held, in stage 1, value m = 8 (t % 2) + i of a thread
+  // with j = 1, so its factor is W_32^m (values of even k had j = 0: factor
+  // one).  The same constants on the same values as stage_tw before the
+  // exchange, without the products by one.
+  static BPM_DEV float2 last_tw(int t, int i) {
+    const bool odd = t & 1;
+    return make_float2(odd ? w32_re(8 + i) : (i == 0 ? 1.f : w32_re(i)),
+                       odd ? w32_im(8 + i) : (i == 0 ? 0.f : w32_im(i)));
+  }
+  template <bool INV>
+  static BPM_DEV void twid_last(float2 (&a)[16], float2 (&b)[16], int t) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float2 w = last_tw(t, i);
+      a[2 * i + 1] = INV ? c_mulc(a[2 * i + 1], w) : c_mul(a[2 * i + 1], w);
+      b[2 * i + 1] = INV ? c_mulc(b[2 * i + 1], w) : c_mul(b[2 * i + 1], w);
     }
   }
 
@@ -185,6 +210,7 @@ struct Fft2Env {
     }
     if constexpr (S > 2) {
       xchg<1, 2, TR>(a, b, buf, stride, estride, t, g);
+      if constexpr (kTwAfter) twid_last<false>(a, b, t);
       sfwd<2>(a, b, tw, t);
     }
     static_assert(S <= 3, "3D transforms up to 4096 points");
@@ -195,6 +221,7 @@ struct Fft2Env {
                           const float2* tw, int t, int g) {
     if constexpr (S > 2) {
       sinv<2>(a, b, tw, t);
+      if constexpr (kTwAfter) twid_last<true>(a, b, t);
       xchg<2, 1, TR>(a, b, buf, stride, estride, t, g);
     }
     if constexpr (S > 1) {
@@ -400,13 +427,23 @@ struct Fft1Env {
   using Gm = Geom<N>;
   static constexpr int T = Gm::T;
   static constexpr int S = Gm::S;
+  static constexpr bool kTwAfter = Fft2Env<N>::kTwAfter;  // as there
 
   template <int s>
   static BPM_DEV void twid(float2 (&a)[16], const float2* tw, int t, bool inv) {
+    if constexpr (kTwAfter && s == 1) return;  // see twid_last
 #pragma unroll
     for (int m = 1; m < 16; ++m) {
       const float2 w = Fft2Env<N>::template stage_tw<s>(tw, t, m);
       a[m] = inv ? c_mulc(a[m], w) : c_mul(a[m], w);
+    }
+  }
+  template <bool INV>
+  static BPM_DEV void twid_last(float2 (&a)[16], int t) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float2 w = Fft2Env<N>::last_tw(t, i);
+      a[2 * i + 1] = INV ? c_mulc(a[2 * i + 1], w) : c_mul(a[2 * i + 1], w);
     }
   }
 
@@ -449,6 +486,7 @@ struct Fft1Env {
     sfwd<1>(a, tw, t);
     if constexpr (S == 3) {
       xchg<1, 2>(a, buf, t, g);
+      if constexpr (kTwAfter) twid_last<false>(a, t);
       sfwd<2>(a, tw, t);
     }
   }
@@ -456,6 +494,7 @@ struct Fft1Env {
   static BPM_DEV void inv(float2 (&a)[16], float2* buf, const float2* tw, int t, int g) {
     if constexpr (S == 3) {
       sinv<2>(a, tw, t);
+      if constexpr (kTwAfter) twid_last<true>(a, t);
       xchg<2, 1>(a, buf, t, g);
     }
     sinv<1>(a, tw, t);

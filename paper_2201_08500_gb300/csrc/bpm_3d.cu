@@ -613,9 +613,11 @@ __global__ void __launch_bounds__(kColTmaThreads, kColTmaBlocksPerSm)
 // (channel, y0) of the pass.  A tile of one envelope is the box {2R floats
 // (R rows of y), NX columns c} of the transposed spectrum [ch][c][y]; the copy
 // engine lays it in shared memory as NX segments of R x 8 bytes, 16-byte
-// chunks swizzled within each 32/64/128-byte span (the span is the segment),
-// so the row reads (one warp: 32 consecutive c of one row) and the output
-// writes spread over all banks.  While a block transforms one tile the next
+// chunks swizzled within each 32/64/128-byte span (the span is the segment).
+// A warp's row read (8 bytes from each of 32 consecutive c of one row) and
+// output write then reach 8 of the 16 eight-byte bank pairs: four wavefronts
+// an access, as many as a 128-bit staging of the same bytes would take,
+// against 16 without the swizzle.  While a block transforms one tile the next
 // one arrives in the stage buffer (one mbarrier phase a tile).  The output
 // tile goes into the rows' exchange regions once the forward transforms are
 // done and leaves by tensor stores; the next tile's first exchange waits

@@ -616,8 +616,9 @@ __global__ void __launch_bounds__(kColTmaThreads, kColTmaBlocksPerSm)
 // chunks swizzled within each 32/64/128-byte span (the span is the segment).
 // A warp's row read (8 bytes from each of 32 consecutive c of one row) and
 // output write then reach 8 of the 16 eight-byte bank pairs: four wavefronts
-// an access, as many as a 128-bit staging of the same bytes would take,
-// against 16 without the swizzle.  While a block transforms one tile the next
+// an access (16 without the swizzle), so a cell's two 64-bit reads cost what
+// the 128-bit store and load of row_pass_kernel's staging cost.  While a
+// block transforms one tile the next
 // one arrives in the stage buffer (one mbarrier phase a tile).  The output
 // tile goes into the rows' exchange regions once the forward transforms are
 // done and leaves by tensor stores; the next tile's first exchange waits

@@ -616,10 +616,10 @@ __global__ void __launch_bounds__(kColTmaThreads, kColTmaBlocksPerSm)
 // chunks swizzled within each 32/64/128-byte span (the span is the segment).
 // A warp's row read (8 bytes from each of 32 consecutive c of one row) and
 // output write then reach 8 of the 16 eight-byte bank pairs: four wavefronts
-// an access (16 without the swizzle), so a cell's two 64-bit reads cost what
-// the 128-bit store and load of row_pass_kernel's staging cost.  While a
-// block transforms one tile the next
-// one arrives in the stage buffer (one mbarrier phase a tile).  The output
+// an access (8 or 16 without the swizzle, at 32- or 64-byte segments), so a
+// cell's two 64-bit reads cost what the 128-bit store and load of
+// row_pass_kernel's staging cost.  While a block transforms one tile the
+// next one arrives in the stage buffer (one mbarrier phase a tile).  The output
 // tile goes into the rows' exchange regions once the forward transforms are
 // done and leaves by tensor stores; the next tile's first exchange waits
 // until those stores have read it.  Stage (2 x NX x R x 8 B) + exchange

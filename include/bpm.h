@@ -204,7 +204,9 @@ BPM_API bpm_status bpm_fetch_reflectivity(bpm_plan plan, double* R, double* T, d
 /* Timing and launch accounting of the most recent bpm_run (after bpm_sync):
  * march_ms is the device time of the march kernel(s) measured with CUDA events
  * on the plan's stream (0 unless enabled with bpm_set_timing), launches is the
- * number of kernels bpm_run enqueued.  The paper has no counterpart.
+ * number of kernels bpm_run enqueued; threads_per_channel, channels_per_block,
+ * blocks and smem_bytes give the 2D march kernel's launch geometry (3D plans:
+ * channels_per_block only, the rest 0).  The paper has no counterpart.
  * bpm_set_timing errors: INVALID_ARG (null plan), CUDA (event creation).
  * bpm_get_stats errors: INVALID_ARG (null argument), STATE (the run has not
  * finished: call bpm_sync first), CUDA. */

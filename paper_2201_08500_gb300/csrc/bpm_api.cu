@@ -354,11 +354,19 @@ bool launch_valid(const bpm_grid& g, int form, int group, int row_threads) {
   return form == 1 && g.split_order == 1 && march_l2_supported(g.nx, group);
 }
 
-// Derived launch quantities of the plan's form.
+// Derived launch quantities of the plan's form (2D: the march kernel's
+// geometry; 3D plans run two passes a step, whose grids the passes size
+// themselves, so only channels_per_block is set).
 void apply_launch(bpm_plan p) {
   p->blocks = (p->n_ch + p->group - 1) / p->group;
-  p->stats.threads_per_channel = march_threads_per_channel(p->grid.nx);
   p->stats.channels_per_block = p->group;
+  if (p->grid.dims == 3) {
+    p->stats.threads_per_channel = 0;
+    p->stats.blocks = 0;
+    p->stats.smem_bytes = 0;
+    return;
+  }
+  p->stats.threads_per_channel = march_threads_per_channel(p->grid.nx);
   p->stats.blocks = p->blocks;
   p->stats.smem_bytes = int(p->form == 1   ? march_l2_smem_bytes(p->grid.nx, p->group)
                             : p->form >= 2 ? march_parked_smem_bytes(p->grid.nx)

@@ -400,7 +400,7 @@ def run_batched(args, world, rank, local, jobs=None):
                     f"{max(w.n_ch for w in ws)} channels, perfect / bent / random strain",
         "cell_updates": cells, "l2": "flushed between timed steps (256 MB write)",
         "form": "one CUDA graph: setup of every instance, persistent work-queue launches "
-                "(13 queues by size and splitting order), time responses",
+                "(14 queues by size and splitting order), time responses",
         "plain": {"value": cells / (ms_plain * 1e-3), "ms_per_step": ms_plain, "steps": steps_p,
                   "form": "per instance: setup kernels, one march launch in its tuned form, "
                           "time response"},

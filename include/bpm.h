@@ -239,7 +239,9 @@ BPM_API bpm_status bpm_get_stats(bpm_plan plan, bpm_stats* out);
  *                      channels_per_block = 1);
  *                      3 = parked with the tables in tensor memory (TMEM)
  *                      instead of L2 (first order or Strang, Nx = 2048, 4096,
- *                      8192, channels_per_block = 1).
+ *                      8192, channels_per_block = 1; first order at Nx =
+ *                      1024 with channels_per_block = 2, the two channels of
+ *                      a block marching independently).
  *                      3D passes: 0 = one block per column group and per row
  *                      tile; 1 = the column pass persistent, each column
  *                      streamed in by a bulk copy; 2 = form 1 plus the

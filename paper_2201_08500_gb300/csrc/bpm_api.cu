@@ -346,6 +346,8 @@ bool launch_valid(const bpm_grid& g, int form, int group, int row_threads) {
   const int maxg = march_max_group(g.nx);
   if (row_threads != 256) return false;
   if (form == 0) return group == 1 || group == maxg;
+  if (form == 3 && g.nx == 1024)  // two channels per block, first order
+    return group == march_parked_group(g.nx, form) && g.split_order == 1;
   if (form == 2 || form == 3)
     return group == 1 &&
            (g.split_order == 1 || (form == 3 && g.split_order == 2) ||
@@ -369,7 +371,7 @@ void apply_launch(bpm_plan p) {
   p->stats.threads_per_channel = march_threads_per_channel(p->grid.nx);
   p->stats.blocks = p->blocks;
   p->stats.smem_bytes = int(p->form == 1   ? march_l2_smem_bytes(p->grid.nx, p->group)
-                            : p->form >= 2 ? march_parked_smem_bytes(p->grid.nx)
+                            : p->form >= 2 ? march_parked_smem_bytes(p->grid.nx, p->form)
                                            : march_smem_bytes(p->grid.nx, p->group));
 }
 
@@ -1054,6 +1056,7 @@ BPM_API bpm_status bpm_tune(const bpm_grid* grid, int n_channels, int steps, bpm
       if (launch_valid(g, 1, maxg, 256)) cand.push_back(bpm_launch{1, maxg, 256, 0.f});
       if (launch_valid(g, 2, 1, 256)) cand.push_back(bpm_launch{2, 1, 256, 0.f});
       if (launch_valid(g, 3, 1, 256)) cand.push_back(bpm_launch{3, 1, 256, 0.f});
+      if (launch_valid(g, 3, 2, 256)) cand.push_back(bpm_launch{3, 2, 256, 0.f});
     }
     for (size_t i = 0; st == BPM_OK && i < cand.size(); ++i) {
       st = bpm_set_launch(p, &cand[i]);
@@ -1320,8 +1323,8 @@ bpm_status enqueue_round(bpm_batch b, RoundSlot& r, int chunk) {
   // then 4096, 2048 and 1024, then the resident small-N queues
   static constexpr int kOrder[kQueueCount] = {
       kQueueTm8192,   kQueueTm8192s2, kQueueBig4,     kQueueTm4096,   kQueueTm4096s2,
-      kQueuePk4096s4, kQueueTm2048,   kQueueTm2048s2, kQueuePk2048s4, kQueuePk1024s4,
-      kQueueSmall,    kQueueSmall2,   kQueueSmall4};
+      kQueuePk4096s4, kQueueTm2048,   kQueueTm2048s2, kQueuePk2048s4, kQueueTm1024,
+      kQueuePk1024s4, kQueueSmall,    kQueueSmall2,   kQueueSmall4};
   int rank[kQueueCount];
   for (int i = 0; i < kQueueCount; ++i) rank[kOrder[i]] = i;
   std::stable_sort(tmp.begin(), tmp.end(), [&rank](const Tmp& x, const Tmp& y) {

@@ -8,7 +8,7 @@
 // 4, 2, 1 channels into the 256-thread block, each with its own shared-memory
 // slot (at most 196 KB).  Nx = 8192 needs 512 threads and runs in a sibling
 // kernel of the same structure, with the parked-envelope body (bpm_parked.cuh).
-// First-order items at Nx >= 2048 run in the tensor-memory kernels below;
+// First-order items at Nx >= 1024 run in the tensor-memory kernels below;
 // second- and fourth-order items in their own instantiations of the two
 // kernels above (one queue per order and size class).  The counter lives in global memory and is
 // cleared before each launch; the queue never waits, so no block can hang.
@@ -119,6 +119,40 @@ __global__ void __launch_bounds__(N / 16, 512 / (N / 16))
   if (threadIdx.x / 32 == 0) tmem_dealloc<P::kCols>(s_tbase);
 }
 
+// First-order items at Nx = 1024 in the tensor-memory parked form with two
+// channels per 128-thread block (Parked<1024, 1, true, true, 2>, the fastest
+// single-plan form there): each channel group of 64 threads takes its own
+// items (its own slot for the counter's answer, its own named barrier), so
+// the two groups march at independent phases; four blocks per SM fill the
+// SM's 512 TMEM columns.
+template <int N>
+__global__ void __launch_bounds__(2 * (N / 16), 512 / (2 * (N / 16)))
+    batch_kernel_tm2(const MarchArgs* __restrict__ plans, const BatchItem* __restrict__ items,
+                     int n_items, int* counter) {
+  using P = Parked<N, 1, true, true, 2>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_item[2];
+  __shared__ uint32_t s_tbase;
+  if (threadIdx.x / 32 == 0) tmem_alloc<P::kCols>(&s_tbase);
+  tmem_sync();
+  const int grp = threadIdx.x / P::T;
+  const int t = threadIdx.x % P::T;
+  const uint32_t tcol = P::tmem_thread(s_tbase, threadIdx.x);
+  unsigned char* gsmem = smem + size_t(grp) * P::group_bytes();
+  for (;;) {
+    P::gsync();
+    if (t == 0) s_item[grp] = atomicAdd(counter, 1);
+    P::gsync();
+    const int it = s_item[grp];
+    if (it >= n_items) break;
+    const BatchItem item = items[it];
+    const MarchArgs& A = plans[item.plan];
+    if (item.ch0 < A.n_ch) P::march_channel(A, item.ch0, gsmem, t, tcol);
+  }
+  tmem_sync();  // both groups are done (their TMEM loads waited)
+  if (threadIdx.x / 32 == 0) tmem_dealloc<P::kCols>(s_tbase);
+}
+
 // Fourth-order items at Nx = 1024, 2048, 4096 in the parked form with both
 // table sets read from L2 (Parked<N, 4>, the fastest single-plan form there):
 // one channel per item, N/16 threads per block, 512/(N/16) blocks per SM.
@@ -145,7 +179,8 @@ __global__ void __launch_bounds__(N / 16, 512 / (N / 16))
 int batch_group(int n) { return n == 8192 ? 1 : kSmallThreads / (n / 16); }
 
 int batch_item_channels(int n, int split_order) {
-  const bool parked = (split_order <= 2 && n >= 2048) || (split_order == 4 && n >= 1024 && n <= 4096);
+  const bool parked = (split_order <= 2 && n >= 2048) || (split_order == 1 && n == 1024) ||
+                      (split_order == 4 && n >= 1024 && n <= 4096);
   return parked ? 1 : batch_group(n);
 }
 
@@ -154,6 +189,7 @@ int batch_queue(int n, int split_order) {
     if (n == 8192) return kQueueTm8192;
     if (n == 4096) return kQueueTm4096;
     if (n == 2048) return kQueueTm2048;
+    if (n == 1024) return kQueueTm1024;
     return kQueueSmall;
   }
   if (split_order == 4) {
@@ -176,7 +212,8 @@ int batch_blocks_per_sm(int queue) {
     case kQueuePk4096s4: return 2;
     case kQueueTm2048:
     case kQueueTm2048s2:
-    case kQueuePk2048s4: return 4;
+    case kQueuePk2048s4:
+    case kQueueTm1024: return 4;
     case kQueuePk1024s4: return 8;
     default: return 1;
   }
@@ -226,6 +263,10 @@ cudaError_t launch_batch(const MarchArgs* plans, const BatchItem* items, int n_i
     case kQueuePk4096s4: pk_launch<4096, 4>(plans, items, n_items, counter, blocks, s); break;
     case kQueuePk2048s4: pk_launch<2048, 4>(plans, items, n_items, counter, blocks, s); break;
     case kQueuePk1024s4: pk_launch<1024, 4>(plans, items, n_items, counter, blocks, s); break;
+    case kQueueTm1024:
+      batch_kernel_tm2<1024><<<blocks, 128, Parked<1024, 1, true, true, 2>::smem_bytes(), s>>>(
+          plans, items, n_items, counter);
+      break;
     case kQueueSmall:
       batch_kernel<1><<<blocks, kSmallThreads, kSmallSmem, s>>>(plans, items, n_items, counter);
       break;
@@ -253,7 +294,9 @@ cudaError_t batch_set_attributes() {
                      cudaFuncSetAttribute(batch_kernel_8192<4>, attr, big),
                      tm_attr<8192, 1>(), tm_attr<4096, 1>(), tm_attr<2048, 1>(),
                      tm_attr<8192, 2>(), tm_attr<4096, 2>(), tm_attr<2048, 2>(),
-                     pk_attr<4096, 4>(), pk_attr<2048, 4>(), pk_attr<1024, 4>()};
+                     pk_attr<4096, 4>(), pk_attr<2048, 4>(), pk_attr<1024, 4>(),
+                     cudaFuncSetAttribute(batch_kernel_tm2<1024>, attr,
+                                          int(Parked<1024, 1, true, true, 2>::smem_bytes()))};
   for (cudaError_t e : r)
     if (e != cudaSuccess) return e;
   return cudaSuccess;

@@ -120,7 +120,7 @@ enum BatchQueue {
   kQueueTm8192 = 0,  // first order, Nx = 8192: parked form, TMEM tables
   kQueueTm4096,      // first order, Nx = 4096: parked form, TMEM tables, 2 blocks / SM
   kQueueTm2048,      // first order, Nx = 2048: parked form, TMEM tables, 4 blocks / SM
-  kQueueSmall,       // first order, Nx <= 1024: resident form, G channels per block
+  kQueueSmall,       // first order, Nx <= 512: resident form, G channels per block
   kQueueSmall2,      // Strang, Nx <= 1024: resident form
   kQueueBig4,        // fourth order, Nx = 8192: parked form, L2 tables (two sets)
   kQueueSmall4,      // fourth order, Nx <= 512: resident form, L2 tables (two sets)
@@ -130,6 +130,8 @@ enum BatchQueue {
   kQueuePk4096s4,    // fourth order, Nx = 4096: parked form, L2 tables, 2 blocks / SM
   kQueuePk2048s4,    // fourth order, Nx = 2048: parked form, L2 tables, 4 blocks / SM
   kQueuePk1024s4,    // fourth order, Nx = 1024: parked form, L2 tables, 8 blocks / SM
+  kQueueTm1024,      // first order, Nx = 1024: parked form, TMEM tables, two channels a
+                     // block, 4 blocks / SM
   kQueueCount
 };
 int batch_group(int n);                               // channels per block of the resident kernels
@@ -167,9 +169,11 @@ cudaError_t march_set_attributes_l2();
 // Parked form (one envelope in registers, one in shared memory) at Nx = 1024..4096:
 // one channel per block, several blocks per SM.
 // (form 2: tables from L2, Nx = 1024..4096; form 3: tables in tensor memory,
-// Nx = 2048..8192).
+// Nx = 1024..8192, two channels per block at 1024).
 bool march_parked_supported(int n, int form);
-size_t march_parked_smem_bytes(int n);
+// Channels per block of a parked form (2 for form 3 at Nx = 1024, else 1).
+int march_parked_group(int n, int form);
+size_t march_parked_smem_bytes(int n, int form);
 cudaError_t launch_march_parked(int n, int form, int blocks, const MarchArgs& a, cudaStream_t s);
 cudaError_t march_set_attributes_parked();
 cudaError_t march_set_attributes_strang();

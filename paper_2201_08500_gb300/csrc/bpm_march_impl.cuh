@@ -13,7 +13,7 @@ namespace bpm {
 // Per-channel march body of a launch form: FORM 0 the register-resident form
 // for N <= 4096 and the parked-envelope form for N = 8192; FORM 1 the L2-table
 // resident form; FORM 2 the parked form at N <= 4096; FORM 3 the parked form
-// with the tables in tensor memory.
+// with the tables in tensor memory (at N = 1024 two channels a block).
 template <int N, int G, int SPLIT, int FORM>
 struct MarchBody {
   using type = Resident<N, G, SPLIT, FORM == 1>;
@@ -29,6 +29,12 @@ struct MarchBody<N, 1, SPLIT, 2> {
 template <int N, int SPLIT>
 struct MarchBody<N, 1, SPLIT, 3> {
   using type = Parked<N, SPLIT, true>;
+};
+// N = 1024: two channels of 64 threads per block, so that a block's 128
+// tensor-memory lanes all hold tables (four blocks of 128 columns per SM).
+template <>
+struct MarchBody<1024, 2, 1, 3> {
+  using type = Parked<1024, 1, true, true, 2>;
 };
 
 // Resident blocks per SM the form is compiled for (128 registers unless 1).

@@ -46,7 +46,12 @@ namespace bpm {
 // TMEM = true keeps each thread's propagator-table slice in tensor memory
 // (bpm_tmem.cuh, 128 columns per thread: 2 envelopes x 16 positions x hi/lo
 // float4) instead of reading it from L2 every step (one table set: SPLIT 1, 2).
-template <int N, int SPLIT = 1, bool TMEM = false, bool WIDE = (N <= 4096)>
+// G channels per block (G x T threads; G > 1 at N = 1024, where a channel's 64
+// threads would leave half of each block's tensor-memory lanes unused): each
+// channel's T threads march their own channels with their own shared-memory
+// region and synchronise through named barrier 1 + its index, so the G
+// channels of a block run at independent phases like separate blocks.
+template <int N, int SPLIT = 1, bool TMEM = false, bool WIDE = (N <= 4096), int G = 1>
 struct Parked {
   static_assert(SPLIT == 1 || SPLIT == 2 || SPLIT == 4, "splitting order");
   static_assert(!TMEM || SPLIT != 4, "TMEM tables: one table set");
@@ -54,9 +59,10 @@ struct Parked {
   static constexpr int T = Gm::T;
   static constexpr int S = Gm::S;
   static constexpr int kTabs = SPLIT == 4 ? 2 : 1;
+  static_assert(G == 1 || (T % 32 == 0 && G * T <= 1024 && G <= 15), "channel groups of whole warps");
   // TMEM columns of the block: warps w and w + 4 share lanes, so each group of
   // four warps takes its own 128 columns
-  static constexpr int kCols = 128 * (T >= 128 ? T / 128 : 1);
+  static constexpr int kCols = 128 * (G * T >= 128 ? G * T / 128 : 1);
   // Wide layout (default at N <= 4096): stage twiddles loaded in 128-bit pairs
   // and the parked envelope in 128-bit slots.  At N = 8192 (128 registers for a
   // 512-thread block) and in the work-queue kernels the narrower per-element
@@ -71,7 +77,18 @@ struct Parked {
   __host__ __device__ static constexpr size_t red_bytes() { return 64 * sizeof(double); }
   // The parks have the exchange buffer's padded size: each serves as the
   // second exchange buffer of the other envelope's transform.
-  __host__ __device__ static constexpr size_t smem_bytes() { return 3 * xbuf_bytes() + red_bytes(); }
+  __host__ __device__ static constexpr size_t group_bytes() { return 3 * xbuf_bytes() + red_bytes(); }
+  __host__ __device__ static constexpr size_t smem_bytes() { return size_t(G) * group_bytes(); }
+
+  // Barrier of this channel's T threads: the block's when G = 1, otherwise
+  // named barrier 1 + (channel group) over T threads.
+  static BPM_DEV void gsync() {
+    if constexpr (G == 1) {
+      __syncthreads();
+    } else {
+      asm volatile("bar.sync %0, %1;" ::"r"(1 + int(threadIdx.x) / T), "r"(T) : "memory");
+    }
+  }
 
   // Per-element stage twiddles (twiddle_order on the host): stage s, output m
   // of thread t at tw_off(s) + (m - 1) LN(s) + t % LN(s).
@@ -169,11 +186,11 @@ struct Parked {
     float2* st = x + P::template base<SF>(t);
     const float2* ld = x + P::template base<ST>(t);
     if constexpr (LEAD) {
-      if constexpr (WARP) __syncwarp(); else __syncthreads();
+      if constexpr (WARP) __syncwarp(); else gsync();
     }
 #pragma unroll
     for (int k = 0; k < 16; ++k) st[P::template off<SF>(k)] = v[k];
-    if constexpr (WARP) __syncwarp(); else __syncthreads();
+    if constexpr (WARP) __syncwarp(); else gsync();
 #pragma unroll
     for (int k = 0; k < 16; ++k) v[k] = ld[P::template off<ST>(k)];
   }
@@ -324,11 +341,11 @@ struct Parked {
   // may still load from x.
   static BPM_DEV void propagate_both(float2 (&v)[16], float2* x, float2* p0, float2* ph,
                                      const float4* gt, uint32_t tcol, const float4* tw, int t) {
-    __syncthreads();  // own-slot accesses of p0 / ph and loads of x are done
+    gsync();  // own-slot accesses of p0 / ph and loads of x are done
     propagate(v, x, p0, gt, tcol, tw, t);  // p0 is free while E0 is in registers
     park(v, p0, t);
     unpark(v, ph, t);
-    __syncthreads();  // x loads and the unparking of ph are done
+    gsync();  // x loads and the unparking of ph are done
     propagate(v, x, ph, gt + N, tcol + 64u, tw, t);
   }
 
@@ -426,7 +443,7 @@ struct Parked {
     // each coupling instead of held in eight registers across the transforms
     ChannelCoef* scf = reinterpret_cast<ChannelCoef*>(red + 32);
     if (SPLIT == 1 && t == 0) scf[0] = A.coef[ch];
-    __syncthreads();
+    gsync();
     const ChannelCoef cfr = A.coef[size_t(ch) * kTabs];
     const ChannelCoef& cf = SPLIT == 1 ? scf[0] : cfr;
     const float4* tw = reinterpret_cast<const float4*>(kWide ? A.twiddle_p : A.twiddle_t);
@@ -474,7 +491,7 @@ struct Parked {
       red[2 * w] = sa;
       red[2 * w + 1] = sb;
     }
-    __syncthreads();
+    gsync();
     if (t == 0) {
       sa = 0.0;
       sb = 0.0;
@@ -486,27 +503,31 @@ struct Parked {
       A.refl[ch] = sb / inc;
       A.trans[ch] = sa / inc;
     }
-    __syncthreads();  // smem reuse by the next channel
+    gsync();  // smem reuse by the next channel
   }
 
   static BPM_DEV void run(const MarchArgs& A, unsigned char* smem) {
-    const int t = threadIdx.x;
+    const int tid = threadIdx.x;
+    const int grp = G == 1 ? 0 : tid / T;  // channel group of this thread
+    const int t = G == 1 ? tid : tid % T;
+    unsigned char* gsmem = G == 1 ? smem : smem + size_t(grp) * group_bytes();
     if constexpr (TMEM) {
       __shared__ uint32_t s_tbase;
-      if (t / 32 == 0) tmem_alloc<kCols>(&s_tbase);
+      if (tid / 32 == 0) tmem_alloc<kCols>(&s_tbase);
       tmem_sync();
       const uint32_t tbase = s_tbase;
-      for (int ch = blockIdx.x; ch < A.n_ch; ch += gridDim.x)
-        march_channel(A, ch, smem, t, tmem_thread(tbase, t));
+      for (int ch = blockIdx.x * G + grp; ch < A.n_ch; ch += gridDim.x * G)
+        march_channel(A, ch, gsmem, t, tmem_thread(tbase, tid));
       tmem_sync();  // every thread's TMEM loads have completed (waited)
-      if (t / 32 == 0) tmem_dealloc<kCols>(tbase);
+      if (tid / 32 == 0) tmem_dealloc<kCols>(tbase);
     } else {
-      for (int ch = blockIdx.x; ch < A.n_ch; ch += gridDim.x) march_channel(A, ch, smem, t);
+      for (int ch = blockIdx.x * G + grp; ch < A.n_ch; ch += gridDim.x * G)
+        march_channel(A, ch, gsmem, t);
     }
   }
 
   static BPM_DEV void run_item(const MarchArgs& A, int ch0, unsigned char* smem) {
-    static_assert(!TMEM, "work-queue items read their tables from L2");
+    static_assert(!TMEM && G == 1, "work-queue items: one channel a block, tables from L2");
     if (ch0 < A.n_ch) march_channel(A, ch0, smem, threadIdx.x);
   }
 };

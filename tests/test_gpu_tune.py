@@ -35,7 +35,8 @@ def fields(w, **form):
 
 @pytest.mark.parametrize("nx,n_ch", [(1024, 611), (2048, 310), (4096, 160), (8192, 40)])
 def test_every_2d_form_gives_identical_fields(nx, n_ch):
-    """Shared-memory (G = 1 and the maximum), L2, parked and parked-TMEM forms."""
+    """Shared-memory (G = 1 and the maximum), L2, parked and parked-TMEM forms
+    (at 1024 two channels per block: 611 channels leave the last block one)."""
     w = deformed_small(nx, nz=48, n_ch=n_ch, seed=31)
     maxg = {1024: 4, 2048: 2, 4096: 1, 8192: 1}[nx]
     ref, _ = fields(w, form=0, channels_per_block=1)
@@ -45,6 +46,8 @@ def test_every_2d_form_gives_identical_fields(nx, n_ch):
         forms.append(dict(form=2, channels_per_block=1))
     if nx >= 2048:
         forms.append(dict(form=3, channels_per_block=1))
+    if nx == 1024:  # tensor-memory tables, two channels per block
+        forms.append(dict(form=3, channels_per_block=2))
     for f in forms:
         got, used = fields(w, **f)
         assert used["form"] == f["form"] and used["channels_per_block"] == f["channels_per_block"]
@@ -143,15 +146,20 @@ def test_forms_a_plan_cannot_run_are_refused():
     with pytest.raises(bpm.BpmError):
         q.set_launch(form=2, channels_per_block=1)   # so is the parked form (and Nx >= 1024)
     with pytest.raises(bpm.BpmError):
-        q.set_launch(form=3, channels_per_block=1)   # the TMEM form needs Nx >= 2048
+        q.set_launch(form=3, channels_per_block=1)   # the TMEM form needs Nx >= 1024
     q.close()
+    r = bpm.plan_from_workload(deformed_small(1024, nz=8, n_ch=4, seed=1))
+    with pytest.raises(bpm.BpmError):
+        r.set_launch(form=3, channels_per_block=1)   # at 1024 it runs two channels a block
+    r.set_launch(form=3, channels_per_block=2)
+    r.close()
 
 
 def test_tuner_keeps_the_fastest_and_later_plans_use_it(tmp_path):
     bpm.tune_clear()
     dx = 0.5e-6
     best, every = bpm.tune(2, 1024, 1, dx, 0.0, dx, 611, steps=8)
-    assert len(every) == 4 and all(f["ms"] > 0 for f in every)  # smem x2, L2, parked
+    assert len(every) == 5 and all(f["ms"] > 0 for f in every)  # smem x2, L2, parked, TMEM
     assert best["ms"] == min(f["ms"] for f in every)
     want = {k: best[k] for k in ("form", "channels_per_block", "row_threads")}
     p = bpm.Plan(2, 1024, 1, 30, dx, 0.0, dx, 611)

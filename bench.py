@@ -737,8 +737,10 @@ def main():
         plan.set_channel_shard(first, w_all.n_ch, shard.pulse_spacing(w_all.omega))
         t_dev = torch.empty((w_all.n_ch, w.plane), dtype=torch.complex128, device="cuda")
     if args.launch_form is not None:
-        plan.set_launch(form=args.launch_form,
-                        channels_per_block=1 if args.launch_form >= 2 else None)
+        # the parked forms run one channel per block; the TMEM form at
+        # Nx = 1024 two
+        cpb = (2 if args.launch_form == 3 and w.nx == 1024 else 1) if args.launch_form >= 2 else None
+        plan.set_launch(form=args.launch_form, channels_per_block=cpb)
     omega = np.ascontiguousarray(w.omega)
     S = np.ascontiguousarray(w.S)
     rows = {}
